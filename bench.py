@@ -1,0 +1,402 @@
+"""Benchmark of the fused LES-LB-MHD time step on GB300 (one JSON line on stdout, rank 0).
+
+Workload (default): the magnetized Kelvin-Helmholtz jet on a 2048 x 2048 periodic grid, plain
+(DNS, Delta = 0) LB-MHD with nu = eta = 5e-4, populations stored in binary32 (f - w and g) with
+binary32 collision; one bench "step" is one time step of the whole grid (one launch of the
+fused kernel).  The populations (906 MB ping-pong) exceed the 129 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the plain FP64 CPU oracle on the host's cores on a bounded sample of
+the same workload (the paper publishes no solver of its own to run).  For N > 1 (torchrun,
+one rank per GPU) every rank runs its own replica (weak scaling, no collective on the data
+path); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM roofline per LES-LB-MHD step vs plain FP64 step, at stated L2 err"
+BYTES_PER_CELL = {"fp32": 216, "fp64": 432}   # 27 populations read + 27 written
+NU = ETA = 5e-4
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the fused FP32 kernel on the
+# 2048^2 workload, from an ncu capture; keyed by the SHA-256 of the kernel source it was taken
+# on, so a changed kernel reports null until it is measured again.
+MEASURED_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=2048, help="grid side (default: the 2048^2 workload)")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--delta", type=float, default=0.0)
+    ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    return ap.parse_args()
+
+
+def kernel_hash() -> str:
+    with open(os.path.join(ROOT, "paper_1705_09807_gb300", "csrc", "lbmhd_step.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def workload_name(n, precision, delta):
+    kind = "dns" if delta == 0 else f"les_delta{delta:g}"
+    return f"kh_jet_{n}x{n}_{kind}_{precision}"
+
+
+# ------------------------------------------------------------------------------ distributed
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, ws: int) -> float:
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[4:]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k + 1] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------ our arm
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def make_sim(n, precision, delta, stream=None):
+    from paper_1705_09807_gb300 import lbmhd
+    from paper_1705_09807_gb300.inputs import kh_jet
+    prec = lbmhd.LBMHD_FP32 if precision == "fp32" else lbmhd.LBMHD_FP64
+    p = lbmhd.lbmhd_params_srt(n, n, NU, ETA, delta, prec)
+    p.cuda_stream = stream
+    fields = kh_jet(n, u0=0.05, delta_frac=1 / 32, b0=0.02, seed=1)
+    return lbmhd.Lbmhd(p, *fields), fields
+
+
+def time_steps(sim, k):
+    """CUDA-event time of k steps on the handle's own stream (ms)."""
+    import torch
+    ext = torch.cuda.ExternalStream(sim.stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(ext)
+    sim.step(k)
+    b.record(ext)
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def e2e_run(n, precision, delta, k):
+    """The user's job through the C ABI with host buffers: init from pinned host fields
+    (host->device copy), k steps, moments back to pinned host arrays (device->host)."""
+    import torch
+    from paper_1705_09807_gb300 import lbmhd
+    from paper_1705_09807_gb300.inputs import kh_jet
+    prec = lbmhd.LBMHD_FP32 if precision == "fp32" else lbmhd.LBMHD_FP64
+    fields = kh_jet(n, u0=0.05, delta_frac=1 / 32, b0=0.02, seed=1)
+    pin_in = [torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy() for _ in range(5)]
+    for d, s in zip(pin_in, fields):
+        d[...] = s
+    pin_out = [torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy() for _ in range(5)]
+    p = lbmhd.lbmhd_params_srt(n, n, NU, ETA, delta, prec)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = lbmhd.lbmhd_init(p, *pin_in)
+    lbmhd.lbmhd_step(h, k)
+    lib = lbmhd.load_library()
+    D = lbmhd._D
+    rc = lib.lbmhd_moments(h, *(o.ctypes.data_as(D) for o in pin_out))
+    t1 = time.perf_counter()
+    lbmhd.lbmhd_free(h)
+    if rc != 0:
+        raise RuntimeError("lbmhd_moments failed")
+    nbytes = 5 * n * n * 8
+    return t1 - t0, nbytes, nbytes
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cpu_oracle_rate(seconds: float, n_tile: int = 256):
+    """Oracle MLUPS on the host cores: a n_tile^2 tile of the same KH jet, same parameters."""
+    import oracle
+    from paper_1705_09807_gb300.inputs import kh_jet
+    cores = os.cpu_count() or 1
+    fields = kh_jet(n_tile, seed=1)
+    f, g = oracle.init(*fields)
+    s, sm = oracle.srt_rates(NU), oracle.rate_from_diffusivity(ETA)
+    t0 = time.perf_counter()
+    f, g = oracle.step(f, g, s, sm, 0.0, 2, nthreads=cores)
+    per = (time.perf_counter() - t0) / 2
+    k = max(1, int(seconds / per))
+    t0 = time.perf_counter()
+    oracle.step(f, g, s, sm, 0.0, k, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return n_tile * n_tile * k / dt / 1e6, cores, k, dt
+
+
+def run_ours(a, rank, ws, local):
+    import torch
+    from paper_1705_09807_gb300 import build
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1705_09807_gb300", "liblbmhd.so")):
+        build.build()
+    barrier(ws)
+    torch.cuda.set_device(local)
+    n, prec, delta = a.n, a.precision, a.delta
+    cells = n * n
+    sim, _ = make_sim(n, prec, delta)
+    sim.step(a.warmup)
+    torch.cuda.synchronize()
+    l0 = sim.launches
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = time_steps(sim, a.steps)
+        barrier(ws)
+        torch.cuda.synchronize()
+    launches = sim.launches - l0
+    ms_max = max_over_ranks(ms, ws)
+    value = ws * cells * a.steps / (ms_max * 1e-3) / 1e6
+    per_launch_s = ms * 1e-3 / a.steps
+    peak, peak_kind = peaks()
+    alg_bytes = BYTES_PER_CELL[prec] * cells
+    achieved = alg_bytes / per_launch_s / 1e9
+    traffic = MEASURED_TRAFFIC.get((kernel_hash(), n, prec, delta))
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": ws,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_max / a.steps, 6),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": workload_name(n, prec, delta), "grid": [n, n], "delta": delta,
+                   "nu": NU, "eta": ETA, "initial_condition": "KH jet U0=0.05 d=N/32 B0=0.02 seed 1",
+                   "storage": "f_i - w_i and g_i in binary32" if prec == "fp32" else "binary64",
+                   "l2_policy": "working set %.0f MB > 129 MB L2, no flush" % (alg_bytes / 1e6),
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "kernel": "fused_step_kernel", "kernel_ms": round(per_launch_s * 1e3, 5)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        e2e_k = min(a.steps, 2000)
+        t, bi, bo = e2e_run(n, prec, delta, e2e_k)
+        out["e2e"] = {"value": round(cells * e2e_k / t / 1e6, 2), "unit": "MLUPS",
+                      "h2d_bytes_per_step": bi / e2e_k, "d2h_bytes_per_step": bo / e2e_k,
+                      "steps": e2e_k, "seconds": round(t, 4),
+                      "note": "init from pinned host fields + steps + moments to pinned host"}
+    if rank == 0 and ws == 1 and not a.quick:
+        out["side"] = side_measurements(n, a)
+        v, cores, k, dt = cpu_oracle_rate(10.0)
+        out["cpu_baseline"] = {"value": round(v, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                               "sample": f"oracle, 256x256 tile of the same KH jet (nu=eta=5e-4, "
+                                         f"Delta=0), {k} steps in {dt:.1f} s, {cores} threads"}
+    sim.free()
+    return out
+
+
+def side_measurements(n, a):
+    """Plain FP64 step on the same grid, the LES form (Delta = 2), and the FP32 error against
+    the FP64 run at fixed step counts."""
+    import torch
+    res = {}
+    k64 = 400
+    sim64, _ = make_sim(n, "fp64", a.delta)
+    sim64.step(20)
+    ms64 = time_steps(sim64, k64)
+    res["fp64_step"] = {"mlups": round(n * n * k64 / (ms64 * 1e-3) / 1e6, 2),
+                        "ms_per_step": round(ms64 / k64, 5),
+                        "hbm_frac": round(BYTES_PER_CELL["fp64"] * n * n / (ms64 * 1e-3 / k64) / 1e9 /
+                                          peaks()[0], 4)}
+    sim64.free()
+    sim32, _ = make_sim(n, "fp32", 2.0)
+    sim32.step(20)
+    msl = time_steps(sim32, 2000)
+    res["fp32_les_delta2"] = {"mlups": round(n * n * 2000 / (msl * 1e-3) / 1e6, 2)}
+    sim32.free()
+    # accuracy of the FP32 form against the FP64 GPU run of the same workload
+    acc = {}
+    s32, _ = make_sim(n, "fp32", a.delta)
+    s64, _ = make_sim(n, "fp64", a.delta)
+    done = 0
+    for t in (1000, 5000):
+        s32.step(t - done)
+        s64.step(t - done)
+        done = t
+        m32, m64 = s32.moments(), s64.moments()
+        acc[str(t)] = {"rho": rel_l2(m32[0], m64[0]), "rho_minus_1": rel_l2(m32[0] - 1, m64[0] - 1),
+                       "u": rel_l2(np.stack(m32[1:3]), np.stack(m64[1:3])),
+                       "B": rel_l2(np.stack(m32[3:5]), np.stack(m64[3:5]))}
+    s32.free()
+    s64.free()
+    res["fp32_rel_l2_vs_fp64_gpu"] = acc
+    # the 256^2 LES grid (L2-resident, launch/latency bound)
+    sl, _ = make_sim(256, "fp32", 2.0)
+    sl.step(64)
+    msl = time_steps(sl, 4096)
+    res["les_256_fp32_delta2"] = {"mlups": round(256 * 256 * 4096 / (msl * 1e-3) / 1e6, 2)}
+    sl.free()
+    torch.cuda.synchronize()
+    return res
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(a, rank, ws):
+    """The FP64 CPU oracle on the host cores; each bench step advances a square tile of the same
+    workload by one time step, the tile sized so the whole run takes about a minute."""
+    import oracle
+    from paper_1705_09807_gb300.inputs import kh_jet
+    oracle.build()
+    cores = os.cpu_count() or 1
+    s, sm = oracle.srt_rates(NU), oracle.rate_from_diffusivity(ETA)
+    # calibrate the oracle's per-cell cost on a 128^2 tile
+    f, g = oracle.init(*kh_jet(128, seed=1))
+    t0 = time.perf_counter()
+    oracle.step(f, g, s, sm, a.delta, 3, nthreads=cores)
+    per_cell = (time.perf_counter() - t0) / 3 / (128 * 128)
+    budget = 60.0
+    side = int(np.sqrt(max(budget / max(a.steps + a.warmup, 1) / per_cell, 9.0)))
+    side = max(64, min(side, a.n))
+    f, g = oracle.init(*kh_jet(side, seed=1))
+    f, g = oracle.step(f, g, s, sm, a.delta, a.warmup, nthreads=cores)
+    t0 = time.perf_counter()
+    oracle.step(f, g, s, sm, a.delta, a.steps, nthreads=cores)  # all K steps in one call
+    dt = time.perf_counter() - t0
+    value = side * side * a.steps / dt / 1e6
+    sample = (f"oracle (plain FP64 C, {cores} threads): {a.steps} steps of a {side}x{side} tile "
+              f"of the same KH jet in one call, after {a.warmup} warm-up steps")
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
+        "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": round(dt * 1e3 / a.steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a.n, a.precision, a.delta), "grid": [a.n, a.n],
+                   "delta": a.delta, "nu": NU, "eta": ETA, "parallelism": "host cores"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(a, rank, ws)), flush=True)
+        return
+    rank, ws, local = dist_setup()
+    out = run_ours(a, rank, ws, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

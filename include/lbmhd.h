@@ -1,0 +1,146 @@
+/*
+ * lbmhd.h - C ABI of the GB300 (sm_103a) fused time step of the filtered (large eddy)
+ * lattice Boltzmann MHD model of Flint & Vahala, "A large eddy lattice Boltzmann
+ * simulation of magnetohydrodynamic turbulence", arXiv:1705.09807.
+ *
+ * The model (Sec. 2, Eqs. LBKinEqn and LBMagEqn): a scalar D2Q9 distribution f_i carries
+ * density and momentum, a vector D2Q9 distribution g_i (two components) carries the magnetic
+ * field.  Moments rho = sum f_i, J = rho u = sum f_i c_i, B = sum g_i (Sec. 2).  One time step
+ * collides in moment space (Eq. Transformation with the matrices T, T_m of Eqs. FluidTMatrix
+ * and MagTMatrix) toward the filtered equilibrium moments of Sec. 2.1 / Sec. 3: the printed
+ * tables Eq. KinMomentEq / MagMomentEq with every nonlinear product expanded to O(Delta^2)
+ * by Eqs. FilterExampleSmall / FilterExampleLarge, filtered density gradients dropped (Sec. 3),
+ * and then streams on a periodic nx x ny grid.  The gradients d_beta J, d_beta B the Delta^2
+ * terms need are finite differences of the current moments.
+ *
+ * Conventions for every function:
+ *  - Return 0 on success or a negative LBMHD_ERR_* code; no C++ exception crosses the ABI.
+ *    lbmhd_last_error() gives a message.
+ *  - Host arrays are owned by the caller and only read or written during the call.
+ *    Device arrays (the *_device variants) are owned by the caller; the call enqueues work
+ *    on the handle's stream and returns without synchronising.
+ *  - Fields are row-major [ny][nx] arrays of double, x fastest.  Populations in canonical
+ *    layout are [q][ny][nx] with q = 0..8 for f_i, 9..17 for g_x,i and 18..26 for g_y,i,
+ *    in the paper's velocity order c_x = {0,1,0,-1,0,1,-1,-1,1}, c_y = {0,0,1,0,-1,1,1,-1,-1}.
+ *  - The handle owns all its device memory; lbmhd_free releases it.  A handle may be used
+ *    from one host thread at a time.
+ */
+#ifndef LBMHD_H
+#define LBMHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBMHD_OK 0
+#define LBMHD_ERR_INVALID (-1)  /* bad argument (checked on the host before any GPU work) */
+#define LBMHD_ERR_CUDA (-2)     /* a CUDA runtime call failed (message has the CUDA error) */
+#define LBMHD_ERR_OOM (-3)      /* device memory allocation failed */
+#define LBMHD_ERR_UNSTABLE (-4) /* diagnostics found NaN/Inf, rho <= 0 or |u| > 0.4 */
+
+/* Storage / arithmetic forms of the populations. */
+#define LBMHD_FP64 0 /* populations stored in binary64, collision in binary64 */
+#define LBMHD_FP32 1 /* f_i - w_i and g_i stored in binary32, collision in binary32 */
+
+/* Finite-difference stencils for d_beta (the paper leaves the discretisation open). */
+#define LBMHD_GRAD_CENTRAL 0   /* (a(x+e_beta) - a(x-e_beta)) / 2 */
+#define LBMHD_GRAD_ISOTROPIC 1 /* sum_i 3 w_i c_i,beta a(x + c_i) over the D2Q9 neighbours */
+
+#define LBMHD_NDIAG 10
+
+typedef struct lbmhd lbmhd_t; /* opaque handle */
+
+/* Problem statement, as the paper states it (Sec. 2 and Sec. 3). */
+typedef struct {
+  int nx, ny;        /* periodic grid, each >= 3 */
+  double s[9];       /* fluid MRT rates s_j for the rows j of T (Eq. LBKinEqn); s[0..2] act
+                        on conserved moments and are ignored; s[3..8] must lie in (0, 2).
+                        nu = 1/(3 s_3) - 1/6 = 1/(3 s_4) - 1/6 and
+                        xi = -1/9 - 1/(9 s_4) - 1/(15 s_7) + 2/(5 s_8) (Sec. 2).
+                        The paper's runs are SRT: all s_j = 1/(3 nu + 1/2) (Sec. 3). */
+  double s_m;        /* magnetic SRT rate (Eq. LBMagEqn), in (0, 2); eta = 1/(3 s_m) - 1/6 */
+  double delta;      /* filter width Delta in lattice units, >= 0; the Delta^2/12 terms of
+                        Sec. 2.1; 0 gives plain (DNS) LB-MHD */
+  int precision;     /* LBMHD_FP64 or LBMHD_FP32 */
+  int grad_stencil;  /* LBMHD_GRAD_CENTRAL or LBMHD_GRAD_ISOTROPIC */
+  void* cuda_stream; /* cudaStream_t to run on; NULL: the handle creates its own stream */
+} lbmhd_params;
+
+/* Fill *p for the paper's SRT runs (Sec. 3): every s_j = 1/(3 nu + 1/2), s_m = 1/(3 eta + 1/2),
+ * central gradients, no stream.  Returns LBMHD_ERR_INVALID for nu, eta <= 0 or a NULL p. */
+int lbmhd_params_srt(lbmhd_params* p, int nx, int ny, double nu, double eta, double delta,
+                     int precision);
+
+/* Create a handle and set the populations to the equilibria Eq. feq and Eq. geq of the
+ * given fields (rho, u = (ux, uy), B = (bx, by)), without Delta terms.  Host input arrays
+ * [ny][nx], copied; synchronises.  On error *out is NULL. */
+int lbmhd_init(lbmhd_t** out, const lbmhd_params* p, const double* rho, const double* ux,
+               const double* uy, const double* bx, const double* by);
+
+/* Same as lbmhd_init with device input arrays [ny][nx] (e.g. torch tensors); the
+ * equilibrium kernel runs on the handle's stream, ordered after earlier work on it. */
+int lbmhd_init_device(lbmhd_t** out, const lbmhd_params* p, const double* rho,
+                      const double* ux, const double* uy, const double* bx, const double* by);
+
+/* Advance nsteps >= 0 time steps (one step = collide, then stream; Sec. 3).  Each step is one
+ * launch of the fused kernel: pull-stream the 27 populations, form rho, J, B and their
+ * gradients, build the filtered equilibria, relax (Eq. LBKinEqn / LBMagEqn in moment space),
+ * store.  Enqueued on the handle's stream; returns without synchronising. */
+int lbmhd_step(lbmhd_t* h, int nsteps);
+
+/* Macroscopic fields of the current (post-stream, pre-collision) populations: rho,
+ * u = J/rho, B.  Host output arrays [ny][nx]; synchronises. */
+int lbmhd_moments(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx, double* by);
+
+/* Same as lbmhd_moments into device arrays [ny][nx]; asynchronous on the handle's stream. */
+int lbmhd_moments_device(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx,
+                         double* by);
+
+/* Current populations in canonical layout [27][ny][nx] (binary64), host array of
+ * 27*nx*ny doubles; synchronises.  For FP32 handles the stored values are widened. */
+int lbmhd_get_populations(lbmhd_t* h, double* pops);
+
+/* Double-precision diagnostics of the current state (host array of LBMHD_NDIAG):
+ * [0] sum rho  [1] sum J_x  [2] sum J_y  [3] sum B_x  [4] sum B_y
+ * [5] sum rho |u|^2 / 2  [6] sum |B|^2 / 2  [7] max |div B| (isotropic stencil)
+ * [8] max |div B| (central stencil)  [9] max |d_beta B_alpha| (isotropic stencil).
+ * Sums are reduced in a fixed order (bitwise reproducible).  Synchronises.  Returns
+ * LBMHD_ERR_UNSTABLE (with out[] filled) if any cell has a NaN/Inf, rho <= 0 or |u| > 0.4. */
+int lbmhd_diagnostics(lbmhd_t* h, double* out);
+
+/* Size in bytes of a checkpoint of this handle's state. */
+size_t lbmhd_state_bytes(const lbmhd_t* h);
+
+/* Copy the raw population state to / from a host buffer of exactly lbmhd_state_bytes(h)
+ * bytes (checkpoint / resume; restoring and stepping reproduces the run bitwise).  The
+ * format is the handle's storage (precision, row pitch); restore only into a handle made
+ * with the same nx, ny and precision.  Both synchronise. */
+int lbmhd_get_state(lbmhd_t* h, void* host_buf, size_t bytes);
+int lbmhd_set_state(lbmhd_t* h, const void* host_buf, size_t bytes);
+
+/* The CUDA stream the handle enqueues its work on (the caller's, or the one it created), as a
+ * cudaStream_t cast to void*; lets a caller record events on it or order other work after it.
+ * NULL for a NULL handle. */
+void* lbmhd_get_stream(const lbmhd_t* h);
+
+/* Number of GPU kernels this handle has launched so far (all kinds). */
+uint64_t lbmhd_launch_count(const lbmhd_t* h);
+
+/* Number of time steps taken since init (or since the last set_state). */
+int64_t lbmhd_step_count(const lbmhd_t* h);
+
+/* Message for the last error on h, or for the calling thread's last handle-less call when
+ * h is NULL.  Never NULL; valid until the next call on the same handle / thread. */
+const char* lbmhd_last_error(const lbmhd_t* h);
+
+/* Release the handle and its device memory (waits for its stream).  NULL is a no-op. */
+void lbmhd_free(lbmhd_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMHD_H */

@@ -1,0 +1,438 @@
+// Host side of the C ABI declared in include/lbmhd.h: argument checks, device memory,
+// stream and graph management, and the launches.  Every function returns a status code;
+// nothing throws across the ABI.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lbmhd.h"
+#include "lbmhd_internal.cuh"
+
+using namespace lbmhd_gpu;
+
+namespace {
+
+constexpr int kGraphSteps = 32;  // steps per captured graph (even: returns to the same buffer)
+
+thread_local std::string g_tls_error;
+
+}  // namespace
+
+struct lbmhd {
+  lbmhd_params p{};
+  int precision = 0;
+  int device = 0;
+  StepGeom geom{};
+  StepCoef coef{};
+  size_t elem = 8;         // bytes per stored population value
+  size_t state_bytes = 0;  // one population copy
+  void* pops[2] = {nullptr, nullptr};
+  int cur = 0;             // copy holding the current state
+  double* fields = nullptr;    // 5 x nx*ny moment fields (moments / diagnostics)
+  double* partials = nullptr;  // diagnostics block partials
+  double* diag_out = nullptr;  // kDiagSlots results
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;  // ordering with the legacy default stream
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  uint64_t launches = 0;
+  int64_t steps = 0;
+  std::string err;
+};
+
+namespace {
+
+int fail(lbmhd_t* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h)
+    h->err = buf;
+  else
+    g_tls_error = buf;
+  return code;
+}
+
+int cuda_fail(lbmhd_t* h, cudaError_t e, const char* what) {
+  return fail(h, e == cudaErrorMemoryAllocation ? LBMHD_ERR_OOM : LBMHD_ERR_CUDA, "%s: %s (%s)",
+              what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define LB_CUDA(h, call)                              \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+int check_params(const lbmhd_params* p) {
+  if (!p) return fail(nullptr, LBMHD_ERR_INVALID, "params is NULL");
+  if (p->nx < 3 || p->ny < 3)
+    return fail(nullptr, LBMHD_ERR_INVALID, "grid %d x %d: both sides must be >= 3", p->nx, p->ny);
+  if ((long long)p->nx * p->ny > (1LL << 31))
+    return fail(nullptr, LBMHD_ERR_INVALID, "grid %d x %d exceeds 2^31 cells", p->nx, p->ny);
+  for (int j = 3; j < 9; ++j)
+    if (!(p->s[j] > 0.0 && p->s[j] < 2.0))
+      return fail(nullptr, LBMHD_ERR_INVALID, "s[%d] = %g outside (0, 2)", j, p->s[j]);
+  if (!(p->s_m > 0.0 && p->s_m < 2.0))
+    return fail(nullptr, LBMHD_ERR_INVALID, "s_m = %g outside (0, 2)", p->s_m);
+  if (!(p->delta >= 0.0) || !std::isfinite(p->delta))
+    return fail(nullptr, LBMHD_ERR_INVALID, "delta = %g must be finite and >= 0", p->delta);
+  if (p->precision != LBMHD_FP64 && p->precision != LBMHD_FP32)
+    return fail(nullptr, LBMHD_ERR_INVALID, "unknown precision %d", p->precision);
+  if (p->grad_stencil != LBMHD_GRAD_CENTRAL && p->grad_stencil != LBMHD_GRAD_ISOTROPIC)
+    return fail(nullptr, LBMHD_ERR_INVALID, "unknown grad_stencil %d", p->grad_stencil);
+  return LBMHD_OK;
+}
+
+void free_all(lbmhd_t* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int i = 0; i < 2; ++i)
+    if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+  for (int i = 0; i < 2; ++i)
+    if (h->pops[i]) cudaFree(h->pops[i]);
+  if (h->fields) cudaFree(h->fields);
+  if (h->partials) cudaFree(h->partials);
+  if (h->diag_out) cudaFree(h->diag_out);
+  if (h->ev_a) cudaEventDestroy(h->ev_a);
+  if (h->ev_b) cudaEventDestroy(h->ev_b);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+// When the handle runs on its own stream, device arrays of the caller are ordered with the
+// legacy default stream (where a caller without streams puts its work) at entry and exit.
+int order_in(lbmhd_t* h) {
+  if (!h->own_stream) return LBMHD_OK;
+  LB_CUDA(h, cudaEventRecord(h->ev_a, cudaStreamLegacy));
+  LB_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_a, 0));
+  return LBMHD_OK;
+}
+int order_out(lbmhd_t* h) {
+  if (!h->own_stream) return LBMHD_OK;
+  LB_CUDA(h, cudaEventRecord(h->ev_b, h->stream));
+  LB_CUDA(h, cudaStreamWaitEvent(cudaStreamLegacy, h->ev_b, 0));
+  return LBMHD_OK;
+}
+
+int create(lbmhd_t** out, const lbmhd_params* p) {
+  if (!out) return fail(nullptr, LBMHD_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int rc = check_params(p);
+  if (rc) return rc;
+  lbmhd_t* h = new (std::nothrow) lbmhd();
+  if (!h) return fail(nullptr, LBMHD_ERR_OOM, "host allocation failed");
+  h->p = *p;
+  h->precision = p->precision;
+  h->elem = p->precision == LBMHD_FP64 ? 8 : 4;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(nullptr, e, "cudaGetDevice");
+  }
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  StepGeom& g = h->geom;
+  g.nx = p->nx;
+  g.ny = p->ny;
+  g.pitch = (p->nx + 31) / 32 * 32;
+  g.plane = (size_t)g.pitch * p->ny;
+  g.band = step_band_rows(p->nx, p->ny, p->precision, sms);
+  // rates scaled by the diagonal of T T^T = (9, 6, 6, 4, 4, 12, 12, 180, 20) (Eq. FluidTMatrix)
+  const double norm[9] = {9, 6, 6, 4, 4, 12, 12, 180, 20};
+  for (int j = 0; j < 9; ++j) h->coef.r[j] = j < 3 ? 0.0 : p->s[j] / norm[j];
+  h->coef.s_m = p->s_m;
+  const double kd = p->delta * p->delta / 12.0;
+  // undivided differences: central a(+1)-a(-1) = 2 d; isotropic 12 d
+  h->coef.kq = p->grad_stencil == LBMHD_GRAD_ISOTROPIC ? kd / 144.0 : kd / 4.0;
+  h->state_bytes = (size_t)kQ * g.plane * h->elem;
+  const size_t ncell = (size_t)p->nx * p->ny;
+#define LB_INIT(call)                 \
+  do {                                \
+    cudaError_t e_ = (call);          \
+    if (e_ != cudaSuccess) {          \
+      int rc_ = cuda_fail(nullptr, e_, #call); \
+      free_all(h);                    \
+      return rc_;                     \
+    }                                 \
+  } while (0)
+  if (p->cuda_stream) {
+    h->stream = (cudaStream_t)p->cuda_stream;
+  } else {
+    LB_INIT(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  LB_INIT(cudaEventCreateWithFlags(&h->ev_a, cudaEventDisableTiming));
+  LB_INIT(cudaEventCreateWithFlags(&h->ev_b, cudaEventDisableTiming));
+  for (int i = 0; i < 2; ++i) LB_INIT(cudaMalloc(&h->pops[i], h->state_bytes));
+  LB_INIT(cudaMalloc(&h->fields, 5 * ncell * sizeof(double)));
+  LB_INIT(cudaMalloc(&h->partials, (size_t)kDiagBlocks * kDiagSlots * sizeof(double)));
+  LB_INIT(cudaMalloc(&h->diag_out, kDiagSlots * sizeof(double)));
+  // zero the pitch padding once so checkpoints are deterministic
+  for (int i = 0; i < 2; ++i) LB_INIT(cudaMemsetAsync(h->pops[i], 0, h->state_bytes, h->stream));
+#undef LB_INIT
+  *out = h;
+  return LBMHD_OK;
+}
+
+int build_graph(lbmhd_t* h, int parity) {
+  cudaGraph_t graph = nullptr;
+  LB_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  int cur = parity;
+  cudaError_t le = cudaSuccess;
+  for (int n = 0; n < kGraphSteps && le == cudaSuccess; ++n) {
+    const int nxt = cur ^ 1;
+    if (h->precision == LBMHD_FP64)
+      le = launch_step_f64((const double*)h->pops[cur], (double*)h->pops[nxt], h->geom, h->coef,
+                           h->p.grad_stencil, h->stream);
+    else
+      le = launch_step_f32((const float*)h->pops[cur], (float*)h->pops[nxt], h->geom, h->coef,
+                           h->p.grad_stencil, h->stream);
+    cur = nxt;
+  }
+  cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+  if (le != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(h, le, "capturing the step graph");
+  }
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamEndCapture");
+  cudaError_t ie = cudaGraphInstantiate(&h->graph[parity], graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    h->graph[parity] = nullptr;
+    return cuda_fail(h, ie, "cudaGraphInstantiate");
+  }
+  return LBMHD_OK;
+}
+
+int one_step(lbmhd_t* h) {
+  const int nxt = h->cur ^ 1;
+  cudaError_t e;
+  if (h->precision == LBMHD_FP64)
+    e = launch_step_f64((const double*)h->pops[h->cur], (double*)h->pops[nxt], h->geom, h->coef,
+                        h->p.grad_stencil, h->stream);
+  else
+    e = launch_step_f32((const float*)h->pops[h->cur], (float*)h->pops[nxt], h->geom, h->coef,
+                        h->p.grad_stencil, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "fused step launch");
+  h->cur = nxt;
+  h->launches += 1;
+  h->steps += 1;
+  return LBMHD_OK;
+}
+
+int check_fields(const double* a, const double* b, const double* c, const double* d,
+                 const double* e) {
+  return a && b && c && d && e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbmhd_params_srt(lbmhd_params* p, int nx, int ny, double nu, double eta, double delta,
+                     int precision) {
+  if (!p) return fail(nullptr, LBMHD_ERR_INVALID, "params is NULL");
+  if (!(nu > 0.0) || !(eta > 0.0))
+    return fail(nullptr, LBMHD_ERR_INVALID, "nu = %g and eta = %g must be > 0", nu, eta);
+  std::memset(p, 0, sizeof *p);
+  p->nx = nx;
+  p->ny = ny;
+  const double s = 1.0 / (3.0 * nu + 0.5);
+  for (int j = 0; j < 9; ++j) p->s[j] = s;
+  p->s_m = 1.0 / (3.0 * eta + 0.5);
+  p->delta = delta;
+  p->precision = precision;
+  p->grad_stencil = LBMHD_GRAD_CENTRAL;
+  p->cuda_stream = nullptr;
+  return LBMHD_OK;
+}
+
+int lbmhd_init(lbmhd_t** out, const lbmhd_params* p, const double* rho, const double* ux,
+               const double* uy, const double* bx, const double* by) {
+  if (!out) return fail(nullptr, LBMHD_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!check_fields(rho, ux, uy, bx, by))
+    return fail(nullptr, LBMHD_ERR_INVALID, "a field pointer is NULL");
+  lbmhd_t* h = nullptr;
+  int rc = create(&h, p);
+  if (rc) return rc;
+  const size_t ncell = (size_t)p->nx * p->ny;
+  const double* src[5] = {rho, ux, uy, bx, by};
+  for (int k = 0; k < 5; ++k) {
+    cudaError_t e = cudaMemcpyAsync(h->fields + k * ncell, src[k], ncell * sizeof(double),
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(nullptr, e, "copying the initial fields to the device");
+      free_all(h);
+      return rc;
+    }
+  }
+  cudaError_t e = launch_init_eq(h->precision, h->pops[0], h->geom, h->fields, h->fields + ncell,
+                                 h->fields + 2 * ncell, h->fields + 3 * ncell,
+                                 h->fields + 4 * ncell, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(nullptr, e, "equilibrium initialisation");
+    free_all(h);
+    return rc;
+  }
+  h->launches += 1;
+  *out = h;
+  return LBMHD_OK;
+}
+
+int lbmhd_init_device(lbmhd_t** out, const lbmhd_params* p, const double* rho,
+                      const double* ux, const double* uy, const double* bx, const double* by) {
+  if (!out) return fail(nullptr, LBMHD_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!check_fields(rho, ux, uy, bx, by))
+    return fail(nullptr, LBMHD_ERR_INVALID, "a field pointer is NULL");
+  lbmhd_t* h = nullptr;
+  int rc = create(&h, p);
+  if (rc) return rc;
+  rc = order_in(h);
+  cudaError_t e = cudaSuccess;
+  if (!rc) e = launch_init_eq(h->precision, h->pops[0], h->geom, rho, ux, uy, bx, by, h->stream);
+  if (!rc && e != cudaSuccess) rc = cuda_fail(h, e, "equilibrium initialisation");
+  if (!rc) rc = order_out(h);
+  if (rc) {
+    g_tls_error = h->err;
+    free_all(h);
+    return rc;
+  }
+  h->launches += 1;
+  *out = h;
+  return LBMHD_OK;
+}
+
+int lbmhd_step(lbmhd_t* h, int nsteps) {
+  if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (nsteps < 0) return fail(h, LBMHD_ERR_INVALID, "nsteps = %d < 0", nsteps);
+  int n = nsteps;
+  // whole graphs of kGraphSteps launches when the handle owns its stream
+  if (h->own_stream && n >= kGraphSteps) {
+    if (!h->graph[h->cur]) {
+      int rc = build_graph(h, h->cur);
+      if (rc) return rc;
+    }
+    while (n >= kGraphSteps) {
+      LB_CUDA(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
+      h->launches += kGraphSteps;
+      h->steps += kGraphSteps;
+      n -= kGraphSteps;  // kGraphSteps is even: h->cur is unchanged
+    }
+  }
+  for (; n > 0; --n) {
+    int rc = one_step(h);
+    if (rc) return rc;
+  }
+  return LBMHD_OK;
+}
+
+int lbmhd_moments_device(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx,
+                         double* by) {
+  if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (!check_fields(rho, ux, uy, bx, by)) return fail(h, LBMHD_ERR_INVALID, "a field pointer is NULL");
+  int rc = order_in(h);
+  if (rc) return rc;
+  LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, rho, ux, uy, bx, by, h->stream));
+  h->launches += 1;
+  return order_out(h);
+}
+
+int lbmhd_moments(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx, double* by) {
+  if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (!check_fields(rho, ux, uy, bx, by)) return fail(h, LBMHD_ERR_INVALID, "a field pointer is NULL");
+  const size_t ncell = (size_t)h->p.nx * h->p.ny;
+  double* f = h->fields;
+  LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, f, f + ncell, f + 2 * ncell,
+                            f + 3 * ncell, f + 4 * ncell, h->stream));
+  h->launches += 1;
+  double* dst[5] = {rho, ux, uy, bx, by};
+  for (int k = 0; k < 5; ++k)
+    LB_CUDA(h, cudaMemcpyAsync(dst[k], f + k * ncell, ncell * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+  LB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return LBMHD_OK;
+}
+
+int lbmhd_get_populations(lbmhd_t* h, double* pops) {
+  if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (!pops) return fail(h, LBMHD_ERR_INVALID, "pops is NULL");
+  const size_t n = (size_t)kQ * h->p.nx * h->p.ny;
+  double* tmp = nullptr;
+  LB_CUDA(h, cudaMallocAsync((void**)&tmp, n * sizeof(double), h->stream));
+  cudaError_t e = launch_populations(h->precision, h->pops[h->cur], h->geom, tmp, h->stream);
+  if (e == cudaSuccess) {
+    h->launches += 1;
+    e = cudaMemcpyAsync(pops, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  }
+  cudaError_t fe = cudaFreeAsync(tmp, h->stream);
+  if (e == cudaSuccess) e = fe;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "exporting populations");
+  return LBMHD_OK;
+}
+
+int lbmhd_diagnostics(lbmhd_t* h, double* out) {
+  if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (!out) return fail(h, LBMHD_ERR_INVALID, "out is NULL");
+  const size_t ncell = (size_t)h->p.nx * h->p.ny;
+  double* f = h->fields;
+  LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, f, f + ncell, f + 2 * ncell,
+                            f + 3 * ncell, f + 4 * ncell, h->stream));
+  LB_CUDA(h, launch_diagnostics(f, h->p.nx, h->p.ny, h->partials, h->diag_out, h->stream));
+  h->launches += 3;
+  double res[kDiagSlots];
+  LB_CUDA(h, cudaMemcpyAsync(res, h->diag_out, sizeof res, cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < LBMHD_NDIAG; ++k) out[k] = res[k];
+  if (res[LBMHD_NDIAG] != 0.0)
+    return fail(h, LBMHD_ERR_UNSTABLE, "unstable state: NaN/Inf, rho <= 0 or |u| > 0.4 after %lld steps",
+                (long long)h->steps);
+  return LBMHD_OK;
+}
+
+size_t lbmhd_state_bytes(const lbmhd_t* h) { return h ? h->state_bytes : 0; }
+
+int lbmhd_get_state(lbmhd_t* h, void* host_buf, size_t bytes) {
+  if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (!host_buf || bytes != h->state_bytes)
+    return fail(h, LBMHD_ERR_INVALID, "state buffer must be %zu bytes", h->state_bytes);
+  LB_CUDA(h, cudaMemcpyAsync(host_buf, h->pops[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return LBMHD_OK;
+}
+
+int lbmhd_set_state(lbmhd_t* h, const void* host_buf, size_t bytes) {
+  if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (!host_buf || bytes != h->state_bytes)
+    return fail(h, LBMHD_ERR_INVALID, "state buffer must be %zu bytes", h->state_bytes);
+  LB_CUDA(h, cudaMemcpyAsync(h->pops[h->cur], host_buf, bytes, cudaMemcpyHostToDevice, h->stream));
+  LB_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->steps = 0;
+  return LBMHD_OK;
+}
+
+void* lbmhd_get_stream(const lbmhd_t* h) { return h ? (void*)h->stream : nullptr; }
+
+uint64_t lbmhd_launch_count(const lbmhd_t* h) { return h ? h->launches : 0; }
+
+int64_t lbmhd_step_count(const lbmhd_t* h) { return h ? h->steps : 0; }
+
+const char* lbmhd_last_error(const lbmhd_t* h) {
+  if (h) return h->err.c_str();
+  return g_tls_error.c_str();
+}
+
+void lbmhd_free(lbmhd_t* h) { free_all(h); }
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+// Auxiliary kernels: equilibrium initialisation, macroscopic moments, canonical population
+// export and double-precision diagnostics.  None of them is on the per-step path.
+#include "lbmhd_internal.cuh"
+
+namespace lbmhd_gpu {
+namespace {
+
+__host__ __device__ constexpr int vx(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int vy(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr double wt(int i) {
+  return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Stored (post-collision) populations whose pull gives the equilibria of the fields:
+// stored f*_i(x) = f_i^eq(fields(x + c_i)), so that f_i(x) = f*_i(x - c_i) = f_i^eq(x).
+// Eq. feq, written as the deviation f_i^eq - w_i; Eq. geq.
+template <typename T>
+__global__ void init_eq_kernel(T* __restrict__ pops, StepGeom g, const double* __restrict__ rho,
+                               const double* __restrict__ ux, const double* __restrict__ uy,
+                               const double* __restrict__ bx, const double* __restrict__ by) {
+  const long n = (long)g.nx * g.ny;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % g.nx), y = (int)(c / g.nx);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const long s = (long)wrapi(y + vy(i), g.ny) * g.nx + wrapi(x + vx(i), g.nx);
+      const double r = rho[s], u = ux[s], v = uy[s], b = bx[s], d = by[s];
+      const double cu = vx(i) * u + vy(i) * v;
+      const double cb = vx(i) * b + vy(i) * d;
+      const double csq = (double)(vx(i) * vx(i) + vy(i) * vy(i));
+      const double w = wt(i);
+      const double fdev = w * (r - 1.0) + w * r * (3.0 * cu + 4.5 * cu * cu - 1.5 * (u * u + v * v)) +
+                          4.5 * w * (0.5 * (b * b + d * d) * csq - cb * cb);
+      const double gx = w * (b + 3.0 * (cu * b - cb * u));
+      const double gy = w * (d + 3.0 * (cu * d - cb * v));
+      const size_t o = (size_t)y * g.pitch + x;
+      pops[(size_t)i * g.plane + o] = (T)fdev;
+      pops[(size_t)(9 + i) * g.plane + o] = (T)gx;
+      pops[(size_t)(18 + i) * g.plane + o] = (T)gy;
+    }
+  }
+}
+
+// Pull the 27 current populations of cell (x, y) in binary64, f as deviations.
+template <typename T>
+__device__ __forceinline__ void pull_cell(const T* __restrict__ pops, const StepGeom& g, int x,
+                                          int y, double v[27]) {
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const int i = q % 9;
+    const int sx = wrapi(x - vx(i), g.nx), sy = wrapi(y - vy(i), g.ny);
+    v[q] = (double)pops[(size_t)q * g.plane + (size_t)sy * g.pitch + sx];
+  }
+}
+
+template <typename T>
+__global__ void moments_kernel(const T* __restrict__ pops, StepGeom g, double* __restrict__ rho,
+                               double* __restrict__ ux, double* __restrict__ uy,
+                               double* __restrict__ bx, double* __restrict__ by) {
+  const long n = (long)g.nx * g.ny;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % g.nx), y = (int)(c / g.nx);
+    double v[27];
+    pull_cell(pops, g, x, y, v);
+    double r = 0, jx = 0, jy = 0, sbx = 0, sby = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      r += v[i];
+      jx += vx(i) * v[i];
+      jy += vy(i) * v[i];
+      sbx += v[9 + i];
+      sby += v[18 + i];
+    }
+    const double rr = 1.0 + r;
+    rho[c] = rr;
+    ux[c] = jx / rr;
+    uy[c] = jy / rr;
+    bx[c] = sbx;
+    by[c] = sby;
+  }
+}
+
+template <typename T>
+__global__ void populations_kernel(const T* __restrict__ pops, StepGeom g, double* __restrict__ out) {
+  const long n = (long)g.nx * g.ny;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % g.nx), y = (int)(c / g.nx);
+    double v[27];
+    pull_cell(pops, g, x, y, v);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) out[(size_t)q * n + c] = q < 9 ? v[q] + wt(q) : v[q];
+  }
+}
+
+// ---- diagnostics ----------------------------------------------------------------------
+constexpr int kDiagThreads = 256;
+
+__device__ __forceinline__ double iso_d(const double* a, int nx, int ny, int x, int y, int axis) {
+  double s = 0.0;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const int c = axis == 0 ? vx(i) : vy(i);
+    if (c == 0) continue;
+    s += 3.0 * wt(i) * c * a[(size_t)wrapi(y + vy(i), ny) * nx + wrapi(x + vx(i), nx)];
+  }
+  return s;
+}
+
+// Slots: 0 sum rho, 1 sum Jx, 2 sum Jy, 3 sum Bx, 4 sum By, 5 sum rho|u|^2/2, 6 sum |B|^2/2,
+// 7 max|div B| isotropic, 8 max|div B| central, 9 max|dB| isotropic, 10 instability flag.
+__global__ void diag_partial_kernel(const double* __restrict__ f, int nx, int ny,
+                                    double* __restrict__ partials) {
+  const long n = (long)nx * ny;
+  const double* rho = f;
+  const double* ux = f + n;
+  const double* uy = f + 2 * n;
+  const double* bx = f + 3 * n;
+  const double* by = f + 4 * n;
+  double acc[kDiagSlots];
+#pragma unroll
+  for (int k = 0; k < kDiagSlots; ++k) acc[k] = 0.0;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % nx), y = (int)(c / nx);
+    const double r = rho[c], u = ux[c], v = uy[c], b = bx[c], d = by[c];
+    acc[0] += r;
+    acc[1] += r * u;
+    acc[2] += r * v;
+    acc[3] += b;
+    acc[4] += d;
+    acc[5] += 0.5 * r * (u * u + v * v);
+    acc[6] += 0.5 * (b * b + d * d);
+    const double dxbx = iso_d(bx, nx, ny, x, y, 0), dybx = iso_d(bx, nx, ny, x, y, 1);
+    const double dxby = iso_d(by, nx, ny, x, y, 0), dyby = iso_d(by, nx, ny, x, y, 1);
+    acc[7] = fmax(acc[7], fabs(dxbx + dyby));
+    const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+    const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+    const double cdiv = 0.5 * (bx[(size_t)y * nx + xp] - bx[(size_t)y * nx + xm] +
+                               by[(size_t)yp * nx + x] - by[(size_t)ym * nx + x]);
+    acc[8] = fmax(acc[8], fabs(cdiv));
+    acc[9] = fmax(acc[9], fmax(fmax(fabs(dxbx), fabs(dybx)), fmax(fabs(dxby), fabs(dyby))));
+    const bool bad = !(isfinite(r) && isfinite(u) && isfinite(v) && isfinite(b) && isfinite(d)) ||
+                     !(r > 0.0) || !(u * u + v * v <= 0.16);
+    if (bad) acc[10] = 1.0;
+  }
+  __shared__ double sh[kDiagSlots][kDiagThreads];
+#pragma unroll
+  for (int k = 0; k < kDiagSlots; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = kDiagThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+#pragma unroll
+      for (int k = 0; k < kDiagSlots; ++k) {
+        const double a = sh[k][threadIdx.x], b = sh[k][threadIdx.x + w];
+        sh[k][threadIdx.x] = (k <= 6) ? a + b : fmax(a, b);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < kDiagSlots) partials[(size_t)blockIdx.x * kDiagSlots + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void diag_final_kernel(const double* __restrict__ partials, int nblocks,
+                                  double* __restrict__ out) {
+  const int k = threadIdx.x;
+  if (k >= kDiagSlots) return;
+  double a = 0.0;
+  for (int b = 0; b < nblocks; ++b) {
+    const double v = partials[(size_t)b * kDiagSlots + k];
+    a = (k <= 6) ? a + v : fmax(a, v);
+  }
+  out[k] = a;
+}
+
+int grid_for(long n, int threads) {
+  long b = (n + threads - 1) / threads;
+  if (b > 152L * 16) b = 152L * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_init_eq(int precision, void* pops, const StepGeom& g, const double* rho,
+                           const double* ux, const double* uy, const double* bx, const double* by,
+                           cudaStream_t s) {
+  const int grid = grid_for((long)g.nx * g.ny, 256);
+  if (precision == 0)
+    init_eq_kernel<double><<<grid, 256, 0, s>>>((double*)pops, g, rho, ux, uy, bx, by);
+  else
+    init_eq_kernel<float><<<grid, 256, 0, s>>>((float*)pops, g, rho, ux, uy, bx, by);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int precision, const void* pops, const StepGeom& g, double* rho,
+                           double* ux, double* uy, double* bx, double* by, cudaStream_t s) {
+  const int grid = grid_for((long)g.nx * g.ny, 256);
+  if (precision == 0)
+    moments_kernel<double><<<grid, 256, 0, s>>>((const double*)pops, g, rho, ux, uy, bx, by);
+  else
+    moments_kernel<float><<<grid, 256, 0, s>>>((const float*)pops, g, rho, ux, uy, bx, by);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_populations(int precision, const void* pops, const StepGeom& g, double* out,
+                               cudaStream_t s) {
+  const int grid = grid_for((long)g.nx * g.ny, 256);
+  if (precision == 0)
+    populations_kernel<double><<<grid, 256, 0, s>>>((const double*)pops, g, out);
+  else
+    populations_kernel<float><<<grid, 256, 0, s>>>((const float*)pops, g, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(const double* fields, int nx, int ny, double* partials, double* out,
+                               cudaStream_t s) {
+  diag_partial_kernel<<<kDiagBlocks, kDiagThreads, 0, s>>>(fields, nx, ny, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_final_kernel<<<1, 32, 0, s>>>(partials, kDiagBlocks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbmhd_gpu

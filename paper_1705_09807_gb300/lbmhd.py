@@ -1,0 +1,298 @@
+"""Python binding of liblbmhd.so (the C ABI in include/lbmhd.h): argument marshalling only.
+
+Every step of the time-stepping path runs in the library's CUDA kernels; this module never
+computes any part of it.  If the shared library is missing it raises instead of falling back
+to anything else.  Host arrays are numpy float64 ``[ny, nx]``; device arrays are torch CUDA
+float64 tensors (PyTorch only supplies device memory and the stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbmhd.so")
+HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "lbmhd.h")
+
+LBMHD_OK = 0
+LBMHD_ERR_INVALID = -1
+LBMHD_ERR_CUDA = -2
+LBMHD_ERR_OOM = -3
+LBMHD_ERR_UNSTABLE = -4
+LBMHD_FP64 = 0
+LBMHD_FP32 = 1
+LBMHD_GRAD_CENTRAL = 0
+LBMHD_GRAD_ISOTROPIC = 1
+LBMHD_NDIAG = 10
+
+DIAG_NAMES = ("mass", "jx", "jy", "bx", "by", "e_kin", "e_mag", "max_div_b_iso",
+              "max_div_b_central", "max_grad_b_iso")
+
+
+class LbmhdParams(ctypes.Structure):
+    """Mirror of ``lbmhd_params`` (include/lbmhd.h)."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("s", ctypes.c_double * 9),
+                ("s_m", ctypes.c_double), ("delta", ctypes.c_double),
+                ("precision", ctypes.c_int), ("grad_stencil", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class LbmhdError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"lbmhd error {code}: {message}")
+        self.code = code
+
+
+class LbmhdUnstable(LbmhdError):
+    def __init__(self, code, message, values):
+        super().__init__(code, message)
+        self.values = values
+
+
+_lib = None
+_lock = threading.Lock()
+_D = ctypes.POINTER(ctypes.c_double)
+_H = ctypes.c_void_p
+
+
+def load_library(path: str | None = None):
+    """Load liblbmhd.so (once).  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with `python -m paper_1705_09807_gb300.build` "
+                               "(there is no fallback implementation)")
+        lib = ctypes.CDLL(p)
+        P = ctypes.POINTER(LbmhdParams)
+        sig = {
+            "lbmhd_params_srt": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+            "lbmhd_init": (ctypes.c_int, [ctypes.POINTER(_H), P, _D, _D, _D, _D, _D]),
+            "lbmhd_init_device": (ctypes.c_int, [ctypes.POINTER(_H), P] + [ctypes.c_void_p] * 5),
+            "lbmhd_step": (ctypes.c_int, [_H, ctypes.c_int]),
+            "lbmhd_moments": (ctypes.c_int, [_H, _D, _D, _D, _D, _D]),
+            "lbmhd_moments_device": (ctypes.c_int, [_H] + [ctypes.c_void_p] * 5),
+            "lbmhd_get_populations": (ctypes.c_int, [_H, _D]),
+            "lbmhd_diagnostics": (ctypes.c_int, [_H, _D]),
+            "lbmhd_state_bytes": (ctypes.c_size_t, [_H]),
+            "lbmhd_get_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
+            "lbmhd_set_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
+            "lbmhd_get_stream": (ctypes.c_void_p, [_H]),
+            "lbmhd_launch_count": (ctypes.c_uint64, [_H]),
+            "lbmhd_step_count": (ctypes.c_int64, [_H]),
+            "lbmhd_last_error": (ctypes.c_char_p, [_H]),
+            "lbmhd_free": (None, [_H]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def header_functions(path: str = HEADER_PATH) -> list:
+    """Names of the functions the public header declares."""
+    with open(path) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbmhd_[a-z_0-9]+)\s*\(", text)))
+
+
+def _err(h) -> str:
+    m = load_library().lbmhd_last_error(h)
+    return m.decode() if m else ""
+
+
+def _check(rc: int, h=None) -> None:
+    if rc != LBMHD_OK:
+        raise LbmhdError(rc, _err(h))
+
+
+def _host(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected an array of shape {shape}, got {a.shape}")
+    return a
+
+
+def _dptr(t, n: int) -> int:
+    """Data pointer of a contiguous CUDA float64 tensor with n elements."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous() and t.numel() == n):
+        raise ValueError("expected a contiguous CUDA float64 tensor of matching size")
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------- functions of the C ABI
+def lbmhd_params_srt(nx, ny, nu, eta, delta, precision=LBMHD_FP64) -> LbmhdParams:
+    p = LbmhdParams()
+    _check(load_library().lbmhd_params_srt(ctypes.byref(p), nx, ny, nu, eta, delta, precision))
+    return p
+
+
+def make_params(nx, ny, s, s_m, delta, precision=LBMHD_FP64, grad_stencil=LBMHD_GRAD_CENTRAL,
+                cuda_stream=None) -> LbmhdParams:
+    p = LbmhdParams()
+    p.nx, p.ny = nx, ny
+    s = np.asarray(s, dtype=np.float64).reshape(9)
+    for j in range(9):
+        p.s[j] = float(s[j])
+    p.s_m, p.delta = float(s_m), float(delta)
+    p.precision, p.grad_stencil = int(precision), int(grad_stencil)
+    p.cuda_stream = cuda_stream
+    return p
+
+
+def lbmhd_init(p: LbmhdParams, rho, ux, uy, bx, by):
+    shape = (p.ny, p.nx)
+    arrs = [_host(a, shape) for a in (rho, ux, uy, bx, by)]
+    h = _H()
+    rc = load_library().lbmhd_init(ctypes.byref(h), ctypes.byref(p),
+                                   *(a.ctypes.data_as(_D) for a in arrs))
+    _check(rc, None)
+    return h
+
+
+def lbmhd_init_device(p: LbmhdParams, rho, ux, uy, bx, by):
+    n = p.nx * p.ny
+    h = _H()
+    rc = load_library().lbmhd_init_device(ctypes.byref(h), ctypes.byref(p),
+                                          *(_dptr(t, n) for t in (rho, ux, uy, bx, by)))
+    _check(rc, None)
+    return h
+
+
+def lbmhd_step(h, nsteps: int) -> None:
+    _check(load_library().lbmhd_step(h, int(nsteps)), h)
+
+
+def lbmhd_moments(h, ny: int, nx: int):
+    outs = [np.empty((ny, nx)) for _ in range(5)]
+    _check(load_library().lbmhd_moments(h, *(o.ctypes.data_as(_D) for o in outs)), h)
+    return tuple(outs)
+
+
+def lbmhd_moments_device(h, outs) -> None:
+    n = outs[0].numel()
+    _check(load_library().lbmhd_moments_device(h, *(_dptr(t, n) for t in outs)), h)
+
+
+def lbmhd_get_populations(h, ny: int, nx: int) -> np.ndarray:
+    out = np.empty((27, ny, nx))
+    _check(load_library().lbmhd_get_populations(h, out.ctypes.data_as(_D)), h)
+    return out
+
+
+def lbmhd_diagnostics(h) -> np.ndarray:
+    out = np.zeros(LBMHD_NDIAG)
+    rc = load_library().lbmhd_diagnostics(h, out.ctypes.data_as(_D))
+    if rc == LBMHD_ERR_UNSTABLE:
+        raise LbmhdUnstable(rc, _err(h), out)
+    _check(rc, h)
+    return out
+
+
+def lbmhd_state_bytes(h) -> int:
+    return int(load_library().lbmhd_state_bytes(h))
+
+
+def lbmhd_get_state(h) -> np.ndarray:
+    buf = np.empty(lbmhd_state_bytes(h), dtype=np.uint8)
+    _check(load_library().lbmhd_get_state(h, buf.ctypes.data, buf.nbytes), h)
+    return buf
+
+
+def lbmhd_set_state(h, buf) -> None:
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(load_library().lbmhd_set_state(h, buf.ctypes.data, buf.nbytes), h)
+
+
+def lbmhd_get_stream(h) -> int:
+    return int(load_library().lbmhd_get_stream(h) or 0)
+
+
+def lbmhd_launch_count(h) -> int:
+    return int(load_library().lbmhd_launch_count(h))
+
+
+def lbmhd_step_count(h) -> int:
+    return int(load_library().lbmhd_step_count(h))
+
+
+def lbmhd_last_error(h=None) -> str:
+    return _err(h)
+
+
+def lbmhd_free(h) -> None:
+    if h is not None and h.value:
+        load_library().lbmhd_free(h)
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class Lbmhd:
+    """Owns one handle; thin sugar over the functions above."""
+
+    def __init__(self, params: LbmhdParams, rho, ux, uy, bx, by, device: bool = False):
+        self.params = params
+        self.nx, self.ny = params.nx, params.ny
+        self.h = (lbmhd_init_device if device else lbmhd_init)(params, rho, ux, uy, bx, by)
+
+    def step(self, n: int) -> "Lbmhd":
+        lbmhd_step(self.h, n)
+        return self
+
+    def moments(self):
+        return lbmhd_moments(self.h, self.ny, self.nx)
+
+    def moments_device(self, outs):
+        lbmhd_moments_device(self.h, outs)
+
+    def populations(self) -> np.ndarray:
+        return lbmhd_get_populations(self.h, self.ny, self.nx)
+
+    def diagnostics(self) -> np.ndarray:
+        return lbmhd_diagnostics(self.h)
+
+    def get_state(self) -> np.ndarray:
+        return lbmhd_get_state(self.h)
+
+    def set_state(self, buf) -> None:
+        lbmhd_set_state(self.h, buf)
+
+    @property
+    def stream(self) -> int:
+        return lbmhd_get_stream(self.h)
+
+    @property
+    def launches(self) -> int:
+        return lbmhd_launch_count(self.h)
+
+    @property
+    def steps(self) -> int:
+        return lbmhd_step_count(self.h)
+
+    def free(self) -> None:
+        if self.h is not None:
+            lbmhd_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

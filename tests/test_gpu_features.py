@@ -1,0 +1,170 @@
+"""GPU checks of the rest of the C ABI: checkpoint/resume, determinism, the device-pointer
+entry points on a caller's stream, diagnostics (conservation, div B, instability status),
+launch accounting and argument errors after a handle exists."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_09807_gb300 import lbmhd
+from paper_1705_09807_gb300.inputs import kh_jet, smooth_random_fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1705_09807_gb300 import build
+    build.build()
+    lbmhd.load_library()
+
+
+def _params(n, precision=lbmhd.LBMHD_FP64, delta=2.0, stream=None, stencil=0):
+    s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
+    return lbmhd.make_params(n, n, s, sm, delta, precision, stencil, stream)
+
+
+@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32])
+def test_checkpoint_resume_bitwise(precision):
+    fields = kh_jet(96, seed=4)
+    with lbmhd.Lbmhd(_params(96, precision), *fields) as sim:
+        sim.step(37)
+        ck = sim.get_state()
+        assert ck.nbytes == lbmhd.lbmhd_state_bytes(sim.h)
+        sim.step(45)
+        a = sim.populations()
+        sim.set_state(ck)
+        assert sim.steps == 0
+        sim.step(45)
+        b = sim.populations()
+    assert np.array_equal(a, b)
+    # restoring into a fresh handle continues the same run
+    with lbmhd.Lbmhd(_params(96, precision), *kh_jet(96, seed=9)) as other:
+        other.set_state(ck)
+        other.step(45)
+        assert np.array_equal(other.populations(), a)
+
+
+def test_runs_are_deterministic_and_graph_free_path_agrees():
+    import torch
+    fields = kh_jet(160, seed=5)
+    with lbmhd.Lbmhd(_params(160), *fields) as s1:
+        s1.step(70)  # own stream: two captured graphs + 6 launches
+        a = s1.populations()
+    with lbmhd.Lbmhd(_params(160), *fields) as s2:
+        s2.step(70)
+        b = s2.populations()
+    st = torch.cuda.Stream()
+    with lbmhd.Lbmhd(_params(160, stream=st.cuda_stream), *fields) as s3:
+        s3.step(70)  # caller's stream: plain launches
+        c = s3.populations()
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_device_entry_points_with_torch_tensors():
+    import torch
+    n = 72
+    fields = smooth_random_fields(n, n, seed=8, amp_u=0.04, amp_b=0.03, amp_rho=0.01)
+    dev = [torch.tensor(a, device="cuda") for a in fields]
+    outs = [torch.empty(n, n, dtype=torch.float64, device="cuda") for _ in range(5)]
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        p = _params(n, stream=torch.cuda.current_stream().cuda_stream)
+        with lbmhd.Lbmhd(p, *dev, device=True) as sim:
+            sim.step(10)
+            sim.moments_device(outs)
+            host = sim.moments()
+    st.synchronize()
+    for o, h in zip(outs, host):
+        assert np.array_equal(o.cpu().numpy(), h)
+    # default stream (handle owns a stream; ordering with the legacy stream is automatic)
+    with lbmhd.Lbmhd(_params(n), *dev, device=True) as sim:
+        sim.step(10)
+        sim.moments_device(outs)
+        torch.cuda.synchronize()
+        for o, h in zip(outs, host):
+            assert np.array_equal(o.cpu().numpy(), h)
+    f, g = oracle.init(*fields)
+    fo, go = oracle.step(f, g, oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002), 2.0, 10)
+    for a, b in zip(host, oracle.moments(fo, go)):
+        assert np.max(np.abs(a - b)) < 1e-13
+
+
+@pytest.mark.parametrize("precision,tol", [(lbmhd.LBMHD_FP64, 1e-13), (lbmhd.LBMHD_FP32, 2e-6)])
+def test_diagnostics_conservation(precision, tol):
+    n = 128
+    fields = kh_jet(n, seed=6)
+    with lbmhd.Lbmhd(_params(n, precision), *fields) as sim:
+        d0 = sim.diagnostics()
+        sim.step(600)
+        d1 = sim.diagnostics()
+    assert abs(d0[0] - n * n) < 1e-9 * n * n
+    assert abs(d1[0] - d0[0]) < tol * n * n                 # mass
+    assert abs(d1[1] - d0[1]) < tol * n * n * 0.05          # momentum
+    assert abs(d1[2] - d0[2]) < tol * n * n * 0.05
+    assert abs(d1[3] - d0[3]) < tol * n * n * 0.02          # magnetic flux
+    assert abs(d1[4] - d0[4]) < tol * n * n * 0.02
+    assert d1[5] < d0[5]                                    # viscous decay of kinetic energy
+    # diagnostics are bitwise reproducible
+    with lbmhd.Lbmhd(_params(n, precision), *fields) as sim:
+        sim.step(600)
+        assert np.array_equal(sim.diagnostics(), d1)
+
+
+def test_one_step_keeps_isotropic_div_b_at_roundoff():
+    """GPU counterpart of the oracle pin: from an equilibrium with a discretely solenoidal B,
+    one step keeps the isotropic divergence at roundoff."""
+    n = 64
+    W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+
+    def iso_d(a, c):
+        return sum(3 * W[i] * c[i] * np.roll(a, (-CY[i], -CX[i]), axis=(0, 1)) for i in range(1, 9))
+
+    rho, ux, uy, _, _ = smooth_random_fields(n, n, seed=5, amp_u=0.05)
+    A = smooth_random_fields(n, n, seed=6, amp_rho=0.5)[0] - 1.0
+    bx, by = iso_d(A, CY), -iso_d(A, CX)
+    with lbmhd.Lbmhd(_params(n, stencil=1), rho, ux, uy, bx, by) as sim:
+        sim.step(1)
+        d = sim.diagnostics()
+    assert d[9] > 1e-3
+    assert d[7] < 1e-14 * d[9]
+
+
+def test_unstable_state_reported_not_faulted():
+    n = 64
+    rho, ux, uy, bx, by = kh_jet(n, u0=0.3, seed=1)
+    s = np.full(9, 1.999)  # nu ~ 1.7e-4: far beyond the stable range for this jet
+    p = lbmhd.make_params(n, n, s, 1.999, 2.0, lbmhd.LBMHD_FP64)
+    with lbmhd.Lbmhd(p, rho, ux, uy, bx, by) as sim:
+        sim.diagnostics()  # the initial state is fine
+        with pytest.raises(lbmhd.LbmhdUnstable) as e:
+            for _ in range(50):
+                sim.step(200)
+                sim.diagnostics()
+        assert e.value.code == lbmhd.LBMHD_ERR_UNSTABLE
+        assert "unstable" in lbmhd.lbmhd_last_error(sim.h)
+        # the context stays usable
+        sim.set_state(np.zeros(lbmhd.lbmhd_state_bytes(sim.h), np.uint8))
+        sim.step(3)
+    z = np.zeros((n, n))
+    with lbmhd.Lbmhd(_params(n), 1 + z, 0.45 + z, z, z, z) as sim:
+        with pytest.raises(lbmhd.LbmhdUnstable):
+            sim.diagnostics()
+
+
+def test_argument_errors_on_a_live_handle():
+    fields = kh_jet(32, seed=1)
+    with lbmhd.Lbmhd(_params(32), *fields) as sim:
+        with pytest.raises(lbmhd.LbmhdError) as e:
+            lbmhd.lbmhd_step(sim.h, -1)
+        assert e.value.code == lbmhd.LBMHD_ERR_INVALID
+        with pytest.raises(lbmhd.LbmhdError):
+            sim.set_state(np.zeros(10, np.uint8))
+        launches = sim.launches
+        sim.step(0)
+        assert sim.launches == launches
+        sim.step(65)
+        assert sim.launches == launches + 65 and sim.steps == 65

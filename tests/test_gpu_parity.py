@@ -1,0 +1,177 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, cell by cell.
+
+Tolerances (written here, derived in the design notes):
+* FP64: populations agree to 1e-13 absolute after short runs (values are O(1); the two codes
+  differ only in rounding order), and rho, u, B to relative L2 <= 1e-12 after the full
+  2000-step Kelvin-Helmholtz run of the 64x64 configuration, whose oracle-vs-oracle floor for a
+  1-ulp change of the initial state stays below 1e-13.
+* FP32 (f - w and g stored in binary32, binary32 collision): relative L2 against the FP64
+  oracle at fixed step counts before the jet saturates, bounds stated per case below.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_09807_gb300 import lbmhd
+from paper_1705_09807_gb300.inputs import kh_jet, smooth_random_fields
+
+pytestmark = pytest.mark.gpu
+NTH = min(8, os.cpu_count() or 1)
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1705_09807_gb300 import build
+    build.build()
+    lbmhd.load_library()
+
+
+def rl2(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def run_pair(fields, s, sm, delta, nsteps, precision=lbmhd.LBMHD_FP64, stencil=0):
+    ny, nx = fields[0].shape
+    f, g = oracle.init(*fields)
+    fo, go = oracle.step(f, g, s, sm, delta, nsteps, stencil=stencil, nthreads=NTH)
+    p = lbmhd.make_params(nx, ny, s, sm, delta, precision, stencil)
+    with lbmhd.Lbmhd(p, *fields) as sim:
+        sim.step(nsteps)
+        pops = sim.populations()
+        mom = sim.moments()
+    ref = np.concatenate([fo, go.reshape(18, ny, nx)])
+    return pops, ref, mom, oracle.moments(fo, go)
+
+
+def mrt_rates(nu):
+    s = oracle.srt_rates(nu)
+    s[5], s[6], s[7], s[8] = 1.35, 1.2, 1.45, 1.1
+    return s
+
+
+CASES = [
+    # (nx, ny, delta, stencil, rates, steps)
+    (64, 64, 2.0, 0, "srt", 7),
+    (64, 64, 0.0, 0, "srt", 12),
+    (33, 17, 2.0, 0, "srt", 9),
+    (33, 17, 2.0, 1, "mrt", 9),
+    (300, 70, 2.0, 0, "mrt", 11),     # 3 strips (128, 128, 44) and several bands, ragged tails
+    (300, 70, 3.0, 1, "srt", 5),
+    (129, 40, 2.0, 1, "srt", 6),      # last strip holds a single column
+    (3, 3, 2.0, 0, "srt", 4),         # smallest grid
+    (4, 7, 2.0, 1, "mrt", 5),
+    (257, 3, 1.0, 0, "srt", 3),
+]
+
+
+@pytest.mark.parametrize("nx,ny,delta,stencil,rates,steps", CASES)
+def test_fp64_populations_match_oracle(nx, ny, delta, stencil, rates, steps):
+    fields = smooth_random_fields(nx, ny, seed=nx * 31 + ny, amp_u=0.05, amp_b=0.04, amp_rho=0.02)
+    s = oracle.srt_rates(0.01) if rates == "srt" else mrt_rates(0.01)
+    sm = oracle.rate_from_diffusivity(0.015)
+    pops, ref, mom, omom = run_pair(fields, s, sm, delta, steps, stencil=stencil)
+    assert np.max(np.abs(pops - ref)) < 1e-13
+    for a, b in zip(mom, omom):
+        assert np.max(np.abs(a - b)) < 1e-13
+
+
+@pytest.mark.parametrize("nsteps", [1, 40])
+def test_fp64_graph_path_many_steps(nsteps):
+    # 40 steps exercises one captured 32-step graph plus single launches
+    fields = kh_jet(96, seed=2, ny=80)
+    s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
+    pops, ref, _, _ = run_pair(fields, s, sm, 2.0, nsteps)
+    assert np.max(np.abs(pops - ref)) < 1e-13
+
+
+@pytest.mark.slow
+def test_fp64_kh_jet_64_full_run():
+    """The 64x64 FP64 configuration, 2000 steps: relative L2 <= 1e-12 on rho, u and B
+    (also on rho - 1), checked at 500, 1000 and 2000 steps."""
+    n = 64
+    fields = kh_jet(n, u0=0.05, delta_frac=1 / 32, b0=0.02, seed=1)
+    s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
+    p = lbmhd.make_params(n, n, s, sm, 2.0, lbmhd.LBMHD_FP64)
+    f, g = oracle.init(*fields)
+    done = 0
+    with lbmhd.Lbmhd(p, *fields) as sim:
+        for t in (500, 1000, 2000):
+            f, g = oracle.step(f, g, s, sm, 2.0, t - done, nthreads=NTH)
+            sim.step(t - done)
+            done = t
+            om = oracle.moments(f, g)
+            gm = sim.moments()
+            assert rl2(gm[0] - 1, om[0] - 1) < 1e-10, t
+            for a, b in zip(gm, om):
+                assert rl2(a, b) < 1e-12, t
+
+
+@pytest.mark.parametrize("steps,tol_u,tol_b", [(100, 2e-6, 2e-6), (500, 5e-6, 5e-6),
+                                               (1000, 2e-5, 2e-5)])
+def test_fp32_kh_jet_64_against_fp64_oracle(steps, tol_u, tol_b):
+    """FP32 storage (f - w and g) with binary32 collision: relative L2 of u and B against the
+    FP64 oracle at fixed step counts before the jet saturates (about step 1800 here)."""
+    n = 64
+    fields = kh_jet(n, seed=1)
+    s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
+    _, _, mom, omom = run_pair(fields, s, sm, 2.0, steps, precision=lbmhd.LBMHD_FP32)
+    assert rl2(mom[0], omom[0]) < 1e-6
+    assert rl2(mom[1], omom[1]) < tol_u and rl2(mom[2], omom[2]) < tol_u
+    assert rl2(mom[3], omom[3]) < tol_b and rl2(mom[4], omom[4]) < tol_b
+
+
+@pytest.mark.parametrize("nx,ny,stencil", [(300, 70, 0), (33, 17, 1), (3, 3, 0)])
+def test_fp32_short_runs_elementwise(nx, ny, stencil):
+    fields = smooth_random_fields(nx, ny, seed=3, amp_u=0.05, amp_b=0.04, amp_rho=0.02)
+    s, sm = mrt_rates(0.01), oracle.rate_from_diffusivity(0.015)
+    pops, ref, _, _ = run_pair(fields, s, sm, 2.0, 6, precision=lbmhd.LBMHD_FP32, stencil=stencil)
+    # binary32 deviations of O(0.1): a few ulp of 0.1 per step
+    assert np.max(np.abs(pops - ref)) < 2e-7
+
+
+def _sampled_full_size(n, precision, delta, nu, warm, tol, seed=1):
+    """Full-size grid in the benchmark's launch configuration: after `warm` steps, one more GPU
+    step must equal the oracle's single-cell collision of the GPU's own state at sampled cells
+    (f_i(x + c_i) after the step = f*_i(x) from the state before it)."""
+    fields = kh_jet(n, seed=seed)
+    s, sm = oracle.srt_rates(nu), oracle.rate_from_diffusivity(nu)
+    p = lbmhd.make_params(n, n, s, sm, delta, precision)
+    with lbmhd.Lbmhd(p, *fields) as sim:
+        sim.step(warm)
+        before = sim.populations()
+        sim.step(1)
+        after = sim.populations()
+    f, g = before[:9], before[9:].reshape(2, 9, n, n)
+    rng = np.random.default_rng(seed)
+    pts = [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (127, 5), (128, n // 2), (n // 2, 0)]
+    pts += [tuple(int(v) for v in rng.integers(0, n, 2)) for _ in range(120)]
+    worst = 0.0
+    for (x, y) in pts:
+        fs, gs = oracle.collide_cell(f, g, s, sm, delta, x, y)
+        for i in range(9):
+            xd, yd = (x + CX[i]) % n, (y + CY[i]) % n
+            worst = max(worst, abs(after[i, yd, xd] - fs[i]), abs(after[9 + i, yd, xd] - gs[0, i]),
+                        abs(after[18 + i, yd, xd] - gs[1, i]))
+    assert worst < tol, worst
+
+
+@pytest.mark.slow
+def test_full_size_2048_fp32_dns_sampled():
+    _sampled_full_size(2048, lbmhd.LBMHD_FP32, 0.0, 5e-4, 50, 1e-7)
+
+
+@pytest.mark.slow
+def test_full_size_2048_fp32_les_sampled():
+    _sampled_full_size(2048, lbmhd.LBMHD_FP32, 2.0, 5e-4, 50, 1e-7)
+
+
+@pytest.mark.slow
+def test_full_size_2048_fp64_les_sampled():
+    _sampled_full_size(2048, lbmhd.LBMHD_FP64, 2.0, 5e-4, 20, 1e-15)
