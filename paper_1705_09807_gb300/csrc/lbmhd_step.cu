@@ -135,32 +135,43 @@ __device__ __forceinline__ void collide(T p[kQ], T rho1, T jx, T jy, T bx, T by,
   p[8] += e78 + (d3 + d6 - d5);
 
   // ---- magnetic: SRT toward Eq. geq with the filtered E ----
-  // g^eq_x,i = w_i (B_x - 3 c_iy E),  g^eq_y,i = w_i (B_y + 3 c_ix E)
+  // g^eq_x,i = w_i (B_x - 3 c_iy E),  g^eq_y,i = w_i (B_y + 3 c_ix E).  The rest population takes
+  // B minus the other eight, so the equilibria sum to B exactly up to one rounding even where
+  // the weights are not representable (binary32): no systematic drift of the magnetic flux.
+  // The update g* = g + s_m (g^eq - g) rounds the small non-equilibrium part, not g itself.
   const T sm = c.sm;
-  const T om = T(1) - sm;
   const T e3 = T(3) * E;
-  const T w0 = T(4.0 / 9.0), wa = T(1.0 / 9.0), wd = T(1.0 / 36.0);
-  const T bxp = bx + e3, bxm = bx - e3, byp = by + e3, bym = by - e3;
-  // x component: c_iy = {0,0,1,0,-1,1,1,-1,-1}
-  p[9] = om * p[9] + sm * (w0 * bx);
-  p[10] = om * p[10] + sm * (wa * bx);
-  p[11] = om * p[11] + sm * (wa * bxm);
-  p[12] = om * p[12] + sm * (wa * bx);
-  p[13] = om * p[13] + sm * (wa * bxp);
-  p[14] = om * p[14] + sm * (wd * bxm);
-  p[15] = om * p[15] + sm * (wd * bxm);
-  p[16] = om * p[16] + sm * (wd * bxp);
-  p[17] = om * p[17] + sm * (wd * bxp);
-  // y component: c_ix = {0,1,0,-1,0,1,-1,-1,1}
-  p[18] = om * p[18] + sm * (w0 * by);
-  p[19] = om * p[19] + sm * (wa * byp);
-  p[20] = om * p[20] + sm * (wa * by);
-  p[21] = om * p[21] + sm * (wa * bym);
-  p[22] = om * p[22] + sm * (wa * by);
-  p[23] = om * p[23] + sm * (wd * byp);
-  p[24] = om * p[24] + sm * (wd * bym);
-  p[25] = om * p[25] + sm * (wd * bym);
-  p[26] = om * p[26] + sm * (wd * byp);
+  const T wa = T(1.0 / 9.0), wd = T(1.0 / 36.0);
+  {
+    // x component: c_iy = {0,0,1,0,-1,1,1,-1,-1}
+    const T ea = wa * bx, em = wa * (bx - e3), ep = wa * (bx + e3);
+    const T dm = wd * (bx - e3), dp = wd * (bx + e3);
+    const T e0 = bx - (((ea + ea) + (em + ep)) + ((dm + dm) + (dp + dp)));
+    p[9] += sm * (e0 - p[9]);
+    p[10] += sm * (ea - p[10]);
+    p[11] += sm * (em - p[11]);
+    p[12] += sm * (ea - p[12]);
+    p[13] += sm * (ep - p[13]);
+    p[14] += sm * (dm - p[14]);
+    p[15] += sm * (dm - p[15]);
+    p[16] += sm * (dp - p[16]);
+    p[17] += sm * (dp - p[17]);
+  }
+  {
+    // y component: c_ix = {0,1,0,-1,0,1,-1,-1,1}
+    const T ea = wa * by, ep = wa * (by + e3), em = wa * (by - e3);
+    const T dp = wd * (by + e3), dm = wd * (by - e3);
+    const T e0 = by - (((ea + ea) + (em + ep)) + ((dm + dm) + (dp + dp)));
+    p[18] += sm * (e0 - p[18]);
+    p[19] += sm * (ep - p[19]);
+    p[20] += sm * (ea - p[20]);
+    p[21] += sm * (em - p[21]);
+    p[22] += sm * (ea - p[22]);
+    p[23] += sm * (dp - p[23]);
+    p[24] += sm * (dm - p[24]);
+    p[25] += sm * (dm - p[25]);
+    p[26] += sm * (dp - p[26]);
+  }
 }
 
 template <typename T>

