@@ -132,6 +132,29 @@ uint64_t lbmhd_launch_count(const lbmhd_t* h);
 /* Number of time steps taken since init (or since the last set_state). */
 int64_t lbmhd_step_count(const lbmhd_t* h);
 
+/* Diagnostics of moment fields that the caller already holds on the device, for callers that
+ * cannot allocate device memory: code that must take every byte from another framework's pool
+ * or arena, code under a fixed memory budget that forbids allocations after start-up, or code
+ * on a path where an allocation would synchronise the device.  The paper has no counterpart;
+ * this is an interface convenience of this library.
+ *
+ * Inputs: rho, ux, uy, bx, by, device arrays [ny][nx] (e.g. from lbmhd_moments_device).
+ * Output: out, a device array of LBMHD_NDIAG + 1 doubles: the LBMHD_NDIAG values of
+ * lbmhd_diagnostics, then 1.0 if any cell has NaN/Inf, rho <= 0 or |u| > 0.4, else 0.0.
+ * Enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream); no synchronisation.
+ *
+ * It calls no cudaMalloc/cudaFree or other allocating routine: its scratch (one partial record
+ * per 4096 cells) is a fixed 352 KiB device array of the library, resident on every GPU that
+ * loads the library until the process exits.  Hence at most 4096 x 4096 = 16,777,216 cells;
+ * larger grids, sides < 3 and NULL pointers return LBMHD_ERR_INVALID (see lbmhd_last_error(NULL)).
+ * The first call on a device looks up that array's device address (once per device, with the
+ * device current); make that first call before any stream capture.  All calls share the one
+ * array, so calls that overlap on the GPU (different streams, no ordering) race and may return
+ * wrong values; each call overwrites every record it reads, so nothing needs clearing. */
+int lbmhd_diagnostics_fields_noalloc(const double* rho, const double* ux, const double* uy,
+                                     const double* bx, const double* by, int nx, int ny,
+                                     double* out, void* stream);
+
 /* Message for the last error on h, or for the calling thread's last handle-less call when
  * h is NULL.  Never NULL; valid until the next call on the same handle / thread. */
 const char* lbmhd_last_error(const lbmhd_t* h);

@@ -23,6 +23,8 @@ thread_local std::string g_tls_error;
 
 }  // namespace
 
+void lbmhd_gpu::set_thread_error(const char* msg) { g_tls_error = msg ? msg : ""; }
+
 struct lbmhd {
   lbmhd_params p{};
   int precision = 0;

@@ -55,4 +55,7 @@ constexpr int kDiagSlots = 11;  // 10 public values + instability flag
 cudaError_t launch_diagnostics(const double* fields, int nx, int ny, double* partials,
                                double* out, cudaStream_t s);
 
+// Store a message for lbmhd_last_error(NULL) on the calling thread (lbmhd_api.cu).
+void set_thread_error(const char* msg);
+
 }  // namespace lbmhd_gpu

@@ -85,6 +85,8 @@ def load_library(path: str | None = None):
             "lbmhd_get_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
             "lbmhd_set_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
             "lbmhd_get_stream": (ctypes.c_void_p, [_H]),
+            "lbmhd_diagnostics_fields_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 5 + [
+                ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
             "lbmhd_launch_count": (ctypes.c_uint64, [_H]),
             "lbmhd_step_count": (ctypes.c_int64, [_H]),
             "lbmhd_last_error": (ctypes.c_char_p, [_H]),
@@ -199,6 +201,17 @@ def lbmhd_diagnostics(h) -> np.ndarray:
         raise LbmhdUnstable(rc, _err(h), out)
     _check(rc, h)
     return out
+
+
+def lbmhd_diagnostics_fields_noalloc(fields, out, stream=None) -> None:
+    """Diagnostics of five device moment fields [ny, nx] into the device tensor ``out``
+    (LBMHD_NDIAG + 1 float64: the values, then the instability flag), allocating nothing on
+    the device; for callers that cannot allocate (see include/lbmhd.h)."""
+    ny, nx = fields[0].shape
+    ptrs = [_dptr(t, nx * ny) for t in fields]
+    rc = load_library().lbmhd_diagnostics_fields_noalloc(*ptrs, nx, ny,
+                                                         _dptr(out, LBMHD_NDIAG + 1), stream)
+    _check(rc, None)
 
 
 def lbmhd_state_bytes(h) -> int:
