@@ -40,6 +40,8 @@ extern "C" {
 #define LBMHD_ERR_CUDA (-2)     /* a CUDA runtime call failed (message has the CUDA error) */
 #define LBMHD_ERR_OOM (-3)      /* device memory allocation failed */
 #define LBMHD_ERR_UNSTABLE (-4) /* diagnostics found NaN/Inf, rho <= 0 or |u| > 0.4 */
+#define LBMHD_ERR_TIMEOUT (-5)  /* a step kernel's pipeline wait ran out (reported by the next
+                                   synchronising call; the state is then invalid) */
 
 /* Storage / arithmetic forms of the populations. */
 #define LBMHD_FP64 0 /* populations stored in binary64, collision in binary64 */

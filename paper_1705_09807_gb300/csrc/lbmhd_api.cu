@@ -1,12 +1,15 @@
 // Host side of the C ABI declared in include/lbmhd.h: argument checks, device memory,
 // stream and graph management, and the launches.  Every function returns a status code;
 // nothing throws across the ABI.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -42,6 +45,8 @@ struct lbmhd {
   bool own_stream = false;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;  // ordering with the legacy default stream
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  CUtensorMap tmap[2];             // 3-D TMA descriptors of the two copies
+  unsigned* err_flag = nullptr;    // device word: set by the step kernel on a pipeline timeout
   uint64_t launches = 0;
   int64_t steps = 0;
   std::string err;
@@ -103,6 +108,7 @@ void free_all(lbmhd_t* h) {
   if (h->fields) cudaFree(h->fields);
   if (h->partials) cudaFree(h->partials);
   if (h->diag_out) cudaFree(h->diag_out);
+  if (h->err_flag) cudaFree(h->err_flag);
   if (h->ev_a) cudaEventDestroy(h->ev_a);
   if (h->ev_b) cudaEventDestroy(h->ev_b);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -121,6 +127,48 @@ int order_out(lbmhd_t* h) {
   if (!h->own_stream) return LBMHD_OK;
   LB_CUDA(h, cudaEventRecord(h->ev_b, h->stream));
   LB_CUDA(h, cudaStreamWaitEvent(cudaStreamLegacy, h->ev_b, 0));
+  return LBMHD_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// 3-D map {pitch, ny, 27} over one population copy, boxes of {kBox, 1, 9} (one row of one
+// 9-plane group, the strip plus 4 columns each side).
+int make_tensor_map(lbmhd_t* h, void* base, CUtensorMap* map) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return fail(nullptr, LBMHD_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const cuuint64_t e = h->elem;
+  cuuint64_t dims[3] = {(cuuint64_t)h->geom.pitch, (cuuint64_t)h->geom.ny, (cuuint64_t)kQ};
+  cuuint64_t strides[2] = {(cuuint64_t)h->geom.pitch * e, (cuuint64_t)h->geom.plane * e};
+  cuuint32_t box[3] = {(cuuint32_t)kBox, 1, 9};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, e == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                   base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(nullptr, LBMHD_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+  return LBMHD_OK;
+}
+
+// Status of the step kernels' pipeline waits (call after synchronising the stream).
+int check_step_status(lbmhd_t* h) {
+  unsigned v = 0;
+  LB_CUDA(h, cudaMemcpy(&v, h->err_flag, sizeof v, cudaMemcpyDeviceToHost));
+  if (v) return fail(h, LBMHD_ERR_TIMEOUT, "a fused-step pipeline wait timed out; the state is invalid");
   return LBMHD_OK;
 }
 
@@ -144,7 +192,7 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
   StepGeom& g = h->geom;
   g.nx = p->nx;
   g.ny = p->ny;
-  g.pitch = (p->nx + 31) / 32 * 32;
+  g.pitch = (p->nx + kXOff + 2 + 31) / 32 * 32;
   g.plane = (size_t)g.pitch * p->ny;
   g.band = step_band_rows(p->nx, p->ny, p->precision, sms);
   // rates scaled by the diagonal of T T^T = (9, 6, 6, 4, 4, 12, 12, 180, 20) (Eq. FluidTMatrix)
@@ -177,7 +225,17 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
   LB_INIT(cudaMalloc(&h->fields, 5 * ncell * sizeof(double)));
   LB_INIT(cudaMalloc(&h->partials, (size_t)kDiagBlocks * kDiagSlots * sizeof(double)));
   LB_INIT(cudaMalloc(&h->diag_out, kDiagSlots * sizeof(double)));
-  // zero the pitch padding once so checkpoints are deterministic
+  LB_INIT(cudaMalloc(&h->err_flag, sizeof(unsigned)));
+  LB_INIT(cudaMemsetAsync(h->err_flag, 0, sizeof(unsigned), h->stream));
+  LB_INIT(prepare_step_kernels());
+  for (int i = 0; i < 2; ++i) {
+    int rc_map = make_tensor_map(h, h->pops[i], &h->tmap[i]);
+    if (rc_map) {
+      free_all(h);
+      return rc_map;
+    }
+  }
+  // zero the row padding once so checkpoints are deterministic
   for (int i = 0; i < 2; ++i) LB_INIT(cudaMemsetAsync(h->pops[i], 0, h->state_bytes, h->stream));
 #undef LB_INIT
   *out = h;
@@ -192,11 +250,11 @@ int build_graph(lbmhd_t* h, int parity) {
   for (int n = 0; n < kGraphSteps && le == cudaSuccess; ++n) {
     const int nxt = cur ^ 1;
     if (h->precision == LBMHD_FP64)
-      le = launch_step_f64((const double*)h->pops[cur], (double*)h->pops[nxt], h->geom, h->coef,
-                           h->p.grad_stencil, h->stream);
+      le = launch_step_f64(h->tmap[cur], (double*)h->pops[nxt], h->geom, h->coef,
+                           h->p.grad_stencil, h->err_flag, h->stream);
     else
-      le = launch_step_f32((const float*)h->pops[cur], (float*)h->pops[nxt], h->geom, h->coef,
-                           h->p.grad_stencil, h->stream);
+      le = launch_step_f32(h->tmap[cur], (float*)h->pops[nxt], h->geom, h->coef,
+                           h->p.grad_stencil, h->err_flag, h->stream);
     cur = nxt;
   }
   cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
@@ -218,11 +276,11 @@ int one_step(lbmhd_t* h) {
   const int nxt = h->cur ^ 1;
   cudaError_t e;
   if (h->precision == LBMHD_FP64)
-    e = launch_step_f64((const double*)h->pops[h->cur], (double*)h->pops[nxt], h->geom, h->coef,
-                        h->p.grad_stencil, h->stream);
+    e = launch_step_f64(h->tmap[h->cur], (double*)h->pops[nxt], h->geom, h->coef,
+                        h->p.grad_stencil, h->err_flag, h->stream);
   else
-    e = launch_step_f32((const float*)h->pops[h->cur], (float*)h->pops[nxt], h->geom, h->coef,
-                        h->p.grad_stencil, h->stream);
+    e = launch_step_f32(h->tmap[h->cur], (float*)h->pops[nxt], h->geom, h->coef,
+                        h->p.grad_stencil, h->err_flag, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "fused step launch");
   h->cur = nxt;
   h->launches += 1;
@@ -363,7 +421,7 @@ int lbmhd_moments(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx, d
     LB_CUDA(h, cudaMemcpyAsync(dst[k], f + k * ncell, ncell * sizeof(double), cudaMemcpyDeviceToHost,
                                h->stream));
   LB_CUDA(h, cudaStreamSynchronize(h->stream));
-  return LBMHD_OK;
+  return check_step_status(h);
 }
 
 int lbmhd_get_populations(lbmhd_t* h, double* pops) {
@@ -381,7 +439,7 @@ int lbmhd_get_populations(lbmhd_t* h, double* pops) {
   if (e == cudaSuccess) e = fe;
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "exporting populations");
-  return LBMHD_OK;
+  return check_step_status(h);
 }
 
 int lbmhd_diagnostics(lbmhd_t* h, double* out) {
@@ -397,6 +455,8 @@ int lbmhd_diagnostics(lbmhd_t* h, double* out) {
   LB_CUDA(h, cudaMemcpyAsync(res, h->diag_out, sizeof res, cudaMemcpyDeviceToHost, h->stream));
   LB_CUDA(h, cudaStreamSynchronize(h->stream));
   for (int k = 0; k < LBMHD_NDIAG; ++k) out[k] = res[k];
+  int st = check_step_status(h);
+  if (st) return st;
   if (res[LBMHD_NDIAG] != 0.0)
     return fail(h, LBMHD_ERR_UNSTABLE, "unstable state: NaN/Inf, rho <= 0 or |u| > 0.4 after %lld steps",
                 (long long)h->steps);
@@ -411,7 +471,7 @@ int lbmhd_get_state(lbmhd_t* h, void* host_buf, size_t bytes) {
     return fail(h, LBMHD_ERR_INVALID, "state buffer must be %zu bytes", h->state_bytes);
   LB_CUDA(h, cudaMemcpyAsync(host_buf, h->pops[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
   LB_CUDA(h, cudaStreamSynchronize(h->stream));
-  return LBMHD_OK;
+  return check_step_status(h);
 }
 
 int lbmhd_set_state(lbmhd_t* h, const void* host_buf, size_t bytes) {

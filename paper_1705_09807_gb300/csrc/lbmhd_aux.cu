@@ -5,21 +5,15 @@
 namespace lbmhd_gpu {
 namespace {
 
-__host__ __device__ constexpr int vx(int i) {
-  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
-}
-__host__ __device__ constexpr int vy(int i) {
-  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
-}
-__host__ __device__ constexpr double wt(int i) {
-  return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-}
+__host__ __device__ constexpr int vx(int i) { return vel_x(i); }
+__host__ __device__ constexpr int vy(int i) { return vel_y(i); }
+__host__ __device__ constexpr double wt(int i) { return lattice_w(i); }
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // Stored (post-collision) populations whose pull gives the equilibria of the fields:
 // stored f*_i(x) = f_i^eq(fields(x + c_i)), so that f_i(x) = f*_i(x - c_i) = f_i^eq(x).
-// Eq. feq, written as the deviation f_i^eq - w_i; Eq. geq.
+// Eq. feq, written as the deviation f_i^eq - w_i; Eq. geq.  Ghost columns written too.
 template <typename T>
 __global__ void init_eq_kernel(T* __restrict__ pops, StepGeom g, const double* __restrict__ rho,
                                const double* __restrict__ ux, const double* __restrict__ uy,
@@ -39,10 +33,15 @@ __global__ void init_eq_kernel(T* __restrict__ pops, StepGeom g, const double* _
                           4.5 * w * (0.5 * (b * b + d * d) * csq - cb * cb);
       const double gx = w * (b + 3.0 * (cu * b - cb * u));
       const double gy = w * (d + 3.0 * (cu * d - cb * v));
-      const size_t o = (size_t)y * g.pitch + x;
-      pops[(size_t)i * g.plane + o] = (T)fdev;
-      pops[(size_t)(9 + i) * g.plane + o] = (T)gx;
-      pops[(size_t)(18 + i) * g.plane + o] = (T)gy;
+      const size_t o = (size_t)y * g.pitch + kXOff + x;
+      const T vals[3] = {(T)fdev, (T)gx, (T)gy};
+#pragma unroll
+      for (int comp = 0; comp < 3; ++comp) {
+        T* pl = pops + (size_t)plane_of(9 * comp + i) * g.plane + o;
+        pl[0] = vals[comp];
+        if (x < 2) pl[g.nx] = vals[comp];          // ghosts of columns 0, 1 at nx, nx + 1
+        if (x >= g.nx - 2) pl[-g.nx] = vals[comp];  // ghosts of columns nx-2, nx-1 at -2, -1
+      }
     }
   }
 }
@@ -55,7 +54,7 @@ __device__ __forceinline__ void pull_cell(const T* __restrict__ pops, const Step
   for (int q = 0; q < 27; ++q) {
     const int i = q % 9;
     const int sx = wrapi(x - vx(i), g.nx), sy = wrapi(y - vy(i), g.ny);
-    v[q] = (double)pops[(size_t)q * g.plane + (size_t)sy * g.pitch + sx];
+    v[q] = (double)pops[(size_t)plane_of(q) * g.plane + (size_t)sy * g.pitch + kXOff + sx];
   }
 }
 

@@ -1,23 +1,55 @@
 // Internal declarations shared by the translation units of liblbmhd.so.
 //
 // HBM layout of the population state (one copy; the handle holds two for ping-pong):
-//   27 planes q = 0..8 (f_i), 9..17 (g_x,i), 18..26 (g_y,i), velocity order of the paper,
-//   each plane ny rows of `pitch` elements (pitch = nx rounded up to 32 elements, so every row
-//   starts on a 128-byte boundary for binary32 and 256-byte for binary64), x fastest.
+//   27 planes, each ny rows of `pitch` elements, x fastest.  Logical column x (0..nx-1) sits at
+//   physical column x + kXOff, so every row's interior starts on a 128-byte (binary32) or
+//   256-byte (binary64) boundary; physical kXOff-2, kXOff-1 and nx+kXOff, nx+kXOff+1 are ghost
+//   copies of logical columns nx-2, nx-1 and 0, 1, kept up to date by every writer, so a row
+//   segment read in one piece already contains the periodic x-neighbours two deep (the pull of
+//   a halo column reaches two columns outside the strip).  pitch = roundup(nx + kXOff + 2, 32).
+//   Plane order groups the populations by c_y (the row they are pulled from):
+//     planes 0..8   c_y = +1: f_2 f_5 f_6, g_x,2 g_x,5 g_x,6, g_y,2 g_y,5 g_y,6
+//     planes 9..17  c_y =  0: f_0 f_1 f_3, g_x,0 g_x,1 g_x,3, g_y,0 g_y,1 g_y,3
+//     planes 18..26 c_y = -1: f_4 f_7 f_8, g_x,4 g_x,7 g_x,8, g_y,4 g_y,7 g_y,8
+//   so the pulled row y of all 27 populations is three boxes: rows y-1, y, y+1 of one
+//   9-plane group each.
 //   The stored values are the POST-COLLISION populations f*_i(x), g*_i(x) of the last step;
 //   the current (post-stream) populations are pulled: f_i(x) = f*_i(x - c_i), periodic.
 //   f is stored as the deviation f_i - w_i from the rest state (rho = 1, u = 0), g as is.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
 
 namespace lbmhd_gpu {
 
-constexpr int kQ = 27;           // populations per cell: 9 (f) + 2 x 9 (g)
+constexpr int kQ = 27;             // populations per cell: 9 (f) + 2 x 9 (g)
 constexpr int kStepThreads = 128;  // threads (= columns) per block of the fused step
-constexpr int kRing = 4;         // rows of moments kept in shared memory
+constexpr int kRing = 4;           // rows of moments kept in shared memory
+constexpr int kXOff = 32;          // physical column of logical x = 0
+constexpr int kBox = kStepThreads + 8;  // columns per staged row segment: strip +- 4
+
+// Paper's D2Q9 velocity order (Sec. 2): c_x = {0,1,0,-1,0,1,-1,-1,1}, c_y = {0,0,1,0,-1,1,1,-1,-1}.
+__host__ __device__ constexpr int vel_x(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int vel_y(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+// group of velocity i (0: c_y = +1, 1: c_y = 0, 2: c_y = -1) and its index inside the group
+__host__ __device__ constexpr int group_of(int i) { return vel_y(i) == 1 ? 0 : (vel_y(i) == 0 ? 1 : 2); }
+__host__ __device__ constexpr int index_in_group(int i) {
+  return (i == 2 || i == 0 || i == 4) ? 0 : ((i == 5 || i == 1 || i == 7) ? 1 : 2);
+}
+// storage plane of canonical population q (0..8 f_i, 9..17 g_x,i, 18..26 g_y,i)
+__host__ __device__ constexpr int plane_of(int q) {
+  return 9 * group_of(q % 9) + 3 * (q / 9) + index_in_group(q % 9);
+}
+__host__ __device__ constexpr double lattice_w(int i) {
+  return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
 
 // Per-launch constants of the fused step, computed on the host in binary64.
 struct StepCoef {
@@ -32,12 +64,17 @@ struct StepGeom {
   int band;           // rows per block
 };
 
-// Fused step launchers (lbmhd_step.cu).  src/dst are distinct population copies.
-cudaError_t launch_step_f64(const double* src, double* dst, const StepGeom& g, const StepCoef& c,
-                            int stencil, cudaStream_t s);
-cudaError_t launch_step_f32(const float* src, float* dst, const StepGeom& g, const StepCoef& c,
-                            int stencil, cudaStream_t s);
+// Fused step launchers (lbmhd_step.cu).  `src` is a 3-D tensor map {pitch, ny, 27} of the
+// source copy (box {kBox, 1, 9}); dst is the other copy.  *err receives 1 if a pipeline wait
+// timed out (the kernel then stops early; the state is not valid).
+cudaError_t launch_step_f64(const CUtensorMap& src, double* dst, const StepGeom& g,
+                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s);
+cudaError_t launch_step_f32(const CUtensorMap& src, float* dst, const StepGeom& g,
+                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s);
+// Rows per block for the grid and precision (one wave of resident blocks when possible).
 int step_band_rows(int nx, int ny, int precision, int num_sms);
+// Opt the step kernels in to their dynamic shared memory (once per process and device).
+cudaError_t prepare_step_kernels();
 
 // Auxiliary kernels (lbmhd_aux.cu).  `precision` selects double / float storage.
 cudaError_t launch_init_eq(int precision, void* pops, const StepGeom& g, const double* rho,
@@ -48,8 +85,8 @@ cudaError_t launch_moments(int precision, const void* pops, const StepGeom& g, d
 cudaError_t launch_populations(int precision, const void* pops, const StepGeom& g, double* out,
                                cudaStream_t s);
 // Diagnostics over the five moment fields (rho, ux, uy, bx, by, each nx*ny, contiguous):
-// block partials into `partials` (nblocks x kDiagSlots doubles), then a single-block fixed-order
-// reduction into out[kDiagSlots] (device).  Returns the number of blocks used via *nblocks.
+// block partials into `partials` (kDiagBlocks x kDiagSlots doubles), then a single-block
+// fixed-order reduction into out[kDiagSlots] (device).
 constexpr int kDiagBlocks = 304;
 constexpr int kDiagSlots = 11;  // 10 public values + instability flag
 cudaError_t launch_diagnostics(const double* fields, int nx, int ny, double* partials,

@@ -4,18 +4,21 @@
 // on the GPU with each population read once from HBM and written once.
 //
 // Work decomposition.  A block of kStepThreads threads owns a strip of that many adjacent
-// columns and a band of `band` rows; each thread owns one column and walks the band from
-// top to bottom.  For row y it
-//   1. pulls the 27 populations of row y+1 (f_i(x) = f*_i(x - c_i), periodic) into registers
-//      and forms their moments, writing J and B of row y+1 to a 4-row shared-memory ring;
-//   2. after one barrier, takes the x-differences of J, B from the ring (and, for the
-//      isotropic stencil, the diagonal neighbours from the rows above and below), and the
-//      y-differences from the moments it holds in registers for rows y-1 and y+1;
-//   3. collides row y (pulled one iteration earlier, still in registers) and stores it.
-// The moments of the two columns just outside the strip and of row band_start-1 are
-// recomputed by the block (halo), so no intermediate ever goes to HBM.  Rows are pitched to
-// 32 elements, so each warp-wide load or store of one plane touches whole 128-byte lines
-// (the +-1 column shifts of the pull straddle two lines; the neighbour warp's reads hit L1/L2).
+// columns and a band of rows; each thread owns one column and the block marches through the
+// band row by row (adjacent bands march in opposite directions, so the two rows a band shares
+// with its neighbour are fetched by both at about the same time and the second fetch hits L2).
+// Rows are staged in shared memory by the tensor-memory accelerator: one elected thread
+// issues, per pulled row r, three 3-D box copies (cp.async.bulk.tensor) of 9 planes x kBox
+// columns each -- source rows r-1, r, r+1 of the three plane groups (planes are grouped by
+// c_y, see lbmhd_internal.cuh) -- completing on the row's mbarrier, NST-2 rows ahead of the
+// row being computed.  For row r the block then
+//   A. waits for row r+1, forms its moments (cell and the two halo columns) into a 4-row
+//      ring of J, B in shared memory;
+//   B. one CTA barrier; the elected thread refills the stage freed by row r-1;
+//   C. takes x- and y-differences of J, B from the ring, collides row r from its stage and
+//      stores 27 coalesced values (plus the ghost columns at the grid's x edges).
+// Every mbarrier wait is bounded in time; on a timeout the block reports through *err,
+// drains its outstanding copies (bounded) and stops.
 //
 // Collision (Sec. 2, Eqs. LBKinEqn, LBMagEqn, Transformation).  Fluid, MRT in moment space:
 //   f* = f - T^{-1} S (T f - Mbar^eq);  T^{-1} = T^T diag(1/|T_j|^2) since T's rows are
@@ -30,59 +33,20 @@
 //   J_a J_b / rho -> (J_a J_b + k G_ab)/rho,  B_a B_b -> B_a B_b + k H_ab,
 //   E -> (J_x B_y - J_y B_x + k (K_xy - K_yx))/rho,   k = Delta^2/12,
 //   G_ab = d_b'J_a d_b'J_b, H_ab = d_b'B_a d_b'B_b, K_ab = d_b'J_a d_b'B_b (sum over b').
+#include <mutex>
+
 #include "lbmhd_internal.cuh"
+#include "lbmhd_ptx.cuh"
 
 namespace lbmhd_gpu {
 namespace {
 
-// Paper's D2Q9 velocity order (Sec. 2): c_x = {0,1,0,-1,0,1,-1,-1,1}, c_y = {0,0,1,0,-1,1,1,-1,-1}.
-__host__ __device__ constexpr int vel_x(int i) {
-  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
-}
-__host__ __device__ constexpr int vel_y(int i) {
-  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
-}
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per mbarrier wait
 
 template <typename T>
 struct KCoef {
   T r3, r4, r5, r6, r7, r8, sm, kq;
 };
-
-template <typename T>
-__device__ __forceinline__ T ld(const T* p) {
-  return __ldg(p);
-}
-
-// Pull the populations of one cell.  cols[0..2] = columns x-1, x, x+1; rows[0..2] = row
-// offsets (row * pitch) of y-1, y, y+1.  Population i comes from (x - c_ix, y - c_iy).
-template <typename T, bool WITH_REST>
-__device__ __forceinline__ void pull27(const T* __restrict__ src, size_t plane, const int cols[3],
-                                       const size_t rows[3], T v[kQ]) {
-#pragma unroll
-  for (int q = 0; q < kQ; ++q) {
-    const int i = q % 9;
-    if (!WITH_REST && q == 0) {  // the rest population f_0 enters neither J nor B
-      v[q] = T(0);
-      continue;
-    }
-    const int col = cols[1 - vel_x(i)];
-    const size_t row = rows[1 - vel_y(i)];
-    v[q] = ld(src + (size_t)q * plane + row + col);
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void moments_jb(const T v[kQ], T& jx, T& jy, T& bx, T& by) {
-  jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
-  jy = (v[2] - v[4]) + (v[5] - v[8]) + (v[6] - v[7]);
-  bx = ((v[9] + v[10]) + (v[11] + v[12])) + ((v[13] + v[14]) + (v[15] + v[16])) + v[17];
-  by = ((v[18] + v[19]) + (v[20] + v[21])) + ((v[22] + v[23]) + (v[24] + v[25])) + v[26];
-}
-
-template <typename T>
-__device__ __forceinline__ T moment_rho_dev(const T v[kQ]) {
-  return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
-}
 
 // Collision of one cell; p[] holds the pulled (current) populations with f as deviations
 // f_i - w_i, and receives the post-collision values.  rho1 = rho - 1.  dJ = undivided
@@ -174,164 +138,200 @@ __device__ __forceinline__ void collide(T p[kQ], T rho1, T jx, T jy, T bx, T by,
   }
 }
 
-template <typename T>
+
+// Shared memory of one block: NST row stages, the moment ring, the stage barriers.
+template <typename T, int NST>
 struct StepSmem {
-  T m[kRing][4][kStepThreads + 2];  // J_x, J_y, B_x, B_y of 4 rows, strip plus 1-column halo
+  static constexpr int kGroupElems = ((9 * kBox * (int)sizeof(T) + 127) / 128 * 128) / (int)sizeof(T);
+  static constexpr int kStageElems = 3 * kGroupElems;
+  static constexpr uint32_t kTxBytes = 3u * 9u * kBox * sizeof(T);  // bytes landing per stage
+  T stage[NST][kStageElems];
+  T ring[kRing][4][kStepThreads + 2];
+  uint64_t full[NST];
+  int abort_flag[2];
 };
 
-template <typename T, int ISO, int MINB>
+template <typename T>
+__device__ __forceinline__ void moments_from(const T* st, int ge, int col, T& rho1, T& jx, T& jy,
+                                             T& bx, T& by) {
+  // pulled population (i, comp) of the cell at box column `col`
+  auto v = [&](int q) -> T {
+    const int i = q % 9;
+    return st[group_of(i) * ge + (3 * (q / 9) + index_in_group(i)) * kBox + col - vel_x(i)];
+  };
+  const T f0 = v(0), f1 = v(1), f2 = v(2), f3 = v(3), f4 = v(4), f5 = v(5), f6 = v(6), f7 = v(7),
+          f8 = v(8);
+  rho1 = ((f0 + f1) + (f2 + f3)) + ((f4 + f5) + (f6 + f7)) + f8;
+  jx = (f1 - f3) + (f5 - f6) + (f8 - f7);
+  jy = (f2 - f4) + (f5 - f8) + (f6 - f7);
+  bx = ((v(9) + v(10)) + (v(11) + v(12))) + ((v(13) + v(14)) + (v(15) + v(16))) + v(17);
+  by = ((v(18) + v(19)) + (v(20) + v(21))) + ((v(22) + v(23)) + (v(24) + v(25))) + v(26);
+}
+
+template <typename T, int ISO, int NST, int MINB>
 __global__ void __launch_bounds__(kStepThreads, MINB)
-    fused_step_kernel(const T* __restrict__ src, T* __restrict__ dst, StepGeom g, KCoef<T> c) {
-  __shared__ StepSmem<T> sh;
+    fused_step_kernel(const __grid_constant__ CUtensorMap src, T* __restrict__ dst, StepGeom g,
+                      KCoef<T> c, unsigned* __restrict__ err) {
+  using SM = StepSmem<T, NST>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // TMA destinations need 128-byte alignment: round the dynamic base up (slack reserved)
+  SM& S = *reinterpret_cast<SM*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+  constexpr int GE = SM::kGroupElems;
+
   const int t = threadIdx.x;
   const int nx = g.nx, ny = g.ny;
   const int x0 = blockIdx.x * kStepThreads;
   const int ncol = min(kStepThreads, nx - x0);
   const bool active = t < ncol;
   const int y0 = blockIdx.y * g.band;
-  const int y1 = min(y0 + g.band, ny);
   if (y0 >= ny) return;  // uniform per block
-
-  const int x = x0 + t;
-  int cols[3];
-  cols[1] = active ? x : x0;
-  cols[0] = cols[1] == 0 ? nx - 1 : cols[1] - 1;
-  cols[2] = cols[1] == nx - 1 ? 0 : cols[1] + 1;
-  // halo duties: thread 0 -> column left of the strip, thread ncol-1 -> column right of it
-  const bool hleft = (t == 0);
-  const bool hright = (t == ncol - 1);
-  int hcl[3], hcr[3];
-  hcl[1] = x0 == 0 ? nx - 1 : x0 - 1;
-  hcl[0] = hcl[1] == 0 ? nx - 1 : hcl[1] - 1;
-  hcl[2] = hcl[1] == nx - 1 ? 0 : hcl[1] + 1;
-  hcr[1] = (x0 + ncol == nx) ? 0 : x0 + ncol;
-  hcr[0] = hcr[1] == 0 ? nx - 1 : hcr[1] - 1;
-  hcr[2] = hcr[1] == nx - 1 ? 0 : hcr[1] + 1;
-  const int si = t + 1;        // shared-memory slot of this column
-  const int sr = ncol + 1;     // slot of the right halo column
-  const size_t pitch = (size_t)g.pitch;
-
-  auto row_offsets = [&](int y, size_t r[3]) {
-    const int ym = y == 0 ? ny - 1 : y - 1;
-    const int yp = y == ny - 1 ? 0 : y + 1;
-    r[0] = (size_t)ym * pitch;
-    r[1] = (size_t)y * pitch;
-    r[2] = (size_t)yp * pitch;
+  const int y1 = min(y0 + g.band, ny);
+  const int L = (y1 - y0) + 2;  // rows staged: the band and one on each side
+  const int dir = (blockIdx.y & 1) ? -1 : 1;
+  // k-th row in march order (k = 0 and L-1 are the neighbours' rows)
+  auto row_of = [&](int k) -> int {
+    int r = dir > 0 ? y0 - 1 + k : y1 - k;
+    if (r < 0) r += ny;
+    if (r >= ny) r -= ny;
+    return r;
   };
-  // moments of the halo columns of row y into ring slot `slot`
-  auto halo = [&](int y, int slot) {
-    if (hleft || hright) {
-      size_t r[3];
-      row_offsets(y, r);
-      T v[kQ], jx, jy, bx, by;
-      if (hleft) {
-        pull27<T, false>(src, g.plane, hcl, r, v);
-        moments_jb(v, jx, jy, bx, by);
-        sh.m[slot][0][0] = jx;
-        sh.m[slot][1][0] = jy;
-        sh.m[slot][2][0] = bx;
-        sh.m[slot][3][0] = by;
-      }
-      if (hright) {
-        pull27<T, false>(src, g.plane, hcr, r, v);
-        moments_jb(v, jx, jy, bx, by);
-        sh.m[slot][0][sr] = jx;
-        sh.m[slot][1][sr] = jy;
-        sh.m[slot][2][sr] = bx;
-        sh.m[slot][3][sr] = by;
-      }
+  auto issue = [&](int k) {
+    const int s = k % NST;
+    const int r = row_of(k);
+    const int ra = r == 0 ? ny - 1 : r - 1;  // c_y = +1 group is pulled from row r - 1
+    const int rc = r == ny - 1 ? 0 : r + 1;  // c_y = -1 group from row r + 1
+    const int cx = x0 + kXOff - 4;           // box covers logical columns x0-4 .. x0+kBox-5
+    mbar_arrive_expect_tx(&S.full[s], SM::kTxBytes);
+    tma_load_3d(&S.stage[s][0], &src, cx, ra, 0, &S.full[s]);
+    tma_load_3d(&S.stage[s][GE], &src, cx, r, 9, &S.full[s]);
+    tma_load_3d(&S.stage[s][2 * GE], &src, cx, rc, 18, &S.full[s]);
+  };
+  auto wait_row = [&](int k) -> bool {
+    return mbar_wait_bounded(&S.full[k % NST], (uint32_t)((k / NST) & 1), kWaitLimitNs);
+  };
+  // moments of staged row k into ring slot k & 3 (own column and the strip's halo columns)
+  T rho_next = T(0);
+  auto ring_moments = [&](int k) {
+    const T* st = S.stage[k % NST];
+    T* rg = &S.ring[k & (kRing - 1)][0][0];
+    constexpr int RS = kStepThreads + 2;
+    T r1, jx, jy, bx, by;
+    if (active) {
+      moments_from(st, GE, t + 4, r1, jx, jy, bx, by);
+      rg[0 * RS + t + 1] = jx;
+      rg[1 * RS + t + 1] = jy;
+      rg[2 * RS + t + 1] = bx;
+      rg[3 * RS + t + 1] = by;
+      rho_next = r1;
+    }
+    if (t == 0) {  // column x0 - 1
+      moments_from(st, GE, 3, r1, jx, jy, bx, by);
+      rg[0 * RS] = jx;
+      rg[1 * RS] = jy;
+      rg[2 * RS] = bx;
+      rg[3 * RS] = by;
+    }
+    if (t == ncol - 1) {  // column x0 + ncol
+      moments_from(st, GE, ncol + 4, r1, jx, jy, bx, by);
+      rg[0 * RS + ncol + 1] = jx;
+      rg[1 * RS + ncol + 1] = jy;
+      rg[2 * RS + ncol + 1] = bx;
+      rg[3 * RS + ncol + 1] = by;
     }
   };
 
-  // ---- prologue: row y0-1 (moments only) and row y0 (populations kept) ----
-  T jxm = 0, jym = 0, bxm = 0, bym = 0;        // row y-1
-  T rho1c = 0, jxc = 0, jyc = 0, bxc = 0, byc = 0;  // row y
-  T p[kQ];
-  {
-    const int ym = y0 == 0 ? ny - 1 : y0 - 1;
-    size_t r[3];
-    if (active) {
-      row_offsets(ym, r);
-      pull27<T, false>(src, g.plane, cols, r, p);
-      moments_jb(p, jxm, jym, bxm, bym);
-      sh.m[0][0][si] = jxm;
-      sh.m[0][1][si] = jym;
-      sh.m[0][2][si] = bxm;
-      sh.m[0][3][si] = bym;
-    }
-    halo(ym, 0);
-    if (active) {
-      row_offsets(y0, r);
-      pull27<T, true>(src, g.plane, cols, r, p);
-      moments_jb(p, jxc, jyc, bxc, byc);
-      rho1c = moment_rho_dev(p);
-      sh.m[1][0][si] = jxc;
-      sh.m[1][1][si] = jyc;
-      sh.m[1][2][si] = bxc;
-      sh.m[1][3][si] = byc;
-    }
-    halo(y0, 1);
+  if (t == 0) {
+    for (int s = 0; s < NST; ++s) mbar_init(&S.full[s], 1);
+    S.abort_flag[0] = 0;
+    S.abort_flag[1] = 0;
+    fence_barrier_init();
+    prefetch_tmap(&src);
   }
+  __syncthreads();
+  const int first = NST < L ? NST : L;
+  if (t == 0)
+    for (int k = 0; k < first; ++k) issue(k);
+  int issued = first;  // meaningful in thread 0 only
 
-  // ---- march down the band ----
-  int it = 1;  // ring index of row y is it & 3
-  for (int y = y0; y < y1; ++y, ++it) {
-    const int yn = y == ny - 1 ? 0 : y + 1;
-    const int sn = (it + 1) & (kRing - 1);
-    const int sc = it & (kRing - 1);
-    const int sp = (it - 1) & (kRing - 1);
-    T q[kQ];
-    T rho1n = 0, jxn = 0, jyn = 0, bxn = 0, byn = 0;
-    if (active) {
-      size_t r[3];
-      row_offsets(yn, r);
-      pull27<T, true>(src, g.plane, cols, r, q);
-      moments_jb(q, jxn, jyn, bxn, byn);
-      rho1n = moment_rho_dev(q);
-      sh.m[sn][0][si] = jxn;
-      sh.m[sn][1][si] = jyn;
-      sh.m[sn][2][si] = bxn;
-      sh.m[sn][3][si] = byn;
-    }
-    halo(yn, sn);
+  // prologue: rows k = 0 and k = 1
+  if (wait_row(0)) ring_moments(0); else S.abort_flag[1] = 1;
+  if (wait_row(1)) ring_moments(1); else S.abort_flag[1] = 1;
+  T rho_cur = rho_next;
+
+  const size_t pitch = (size_t)g.pitch;
+  for (int m = 1; m <= L - 2; ++m) {
+    // A: moments of the next row
+    if (wait_row(m + 1)) ring_moments(m + 1); else S.abort_flag[m & 1] = 1;
+    // B
     __syncthreads();
+    if (S.abort_flag[m & 1]) {
+      if (t == 0) {
+        atomicOr(err, 1u);
+        for (int k = m + 1; k < issued; ++k) wait_row(k);  // drain copies still in flight
+      }
+      return;
+    }
+    if (t == 0 && m - 1 + NST < L) {
+      fence_proxy_async_smem();
+      issue(m - 1 + NST);
+      ++issued;
+    }
+    // C: gradients, collision and store of row m
     if (active) {
+      constexpr int RS = kStepThreads + 2;
+      const T* rc = &S.ring[m & (kRing - 1)][0][0];
+      const T* rn = &S.ring[(dir > 0 ? m + 1 : m - 1) & (kRing - 1)][0][0];  // row y + 1
+      const T* rs = &S.ring[(dir > 0 ? m - 1 : m + 1) & (kRing - 1)][0][0];  // row y - 1
+      const int si = t + 1;
       T dJ[4], dB[4];
       if (ISO) {
-        // undivided isotropic differences: 4 (a_E - a_W) + (a_NE - a_NW) + (a_SE - a_SW)
-        // and 4 (a_N - a_S) + (a_NE - a_SE) + (a_NW - a_SW); their scale 1/12 is in kq
+        // undivided isotropic differences (scale 1/12 in kq):
+        // 4 (a_E - a_W) + (a_NE - a_NW) + (a_SE - a_SW),  4 (a_N - a_S) + (a_NE - a_SE) + (a_NW - a_SW)
         T dx[4], dy[4];
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-          const T e = sh.m[sc][f][si + 1], w = sh.m[sc][f][si - 1];
-          const T ne = sh.m[sn][f][si + 1], nw = sh.m[sn][f][si - 1], nn = sh.m[sn][f][si];
-          const T se = sh.m[sp][f][si + 1], sw = sh.m[sp][f][si - 1], ss = sh.m[sp][f][si];
+          const T e = rc[f * RS + si + 1], w = rc[f * RS + si - 1];
+          const T ne = rn[f * RS + si + 1], nw = rn[f * RS + si - 1], nn = rn[f * RS + si];
+          const T se = rs[f * RS + si + 1], sw = rs[f * RS + si - 1], ss = rs[f * RS + si];
           dx[f] = T(4) * (e - w) + ((ne - nw) + (se - sw));
           dy[f] = T(4) * (nn - ss) + ((ne - se) + (nw - sw));
         }
         dJ[0] = dx[0]; dJ[1] = dy[0]; dJ[2] = dx[1]; dJ[3] = dy[1];
         dB[0] = dx[2]; dB[1] = dy[2]; dB[2] = dx[3]; dB[3] = dy[3];
       } else {
-        // undivided central differences a(+1) - a(-1); their scale 1/2 is in kq
-        dJ[0] = sh.m[sc][0][si + 1] - sh.m[sc][0][si - 1];
-        dJ[1] = jxn - jxm;
-        dJ[2] = sh.m[sc][1][si + 1] - sh.m[sc][1][si - 1];
-        dJ[3] = jyn - jym;
-        dB[0] = sh.m[sc][2][si + 1] - sh.m[sc][2][si - 1];
-        dB[1] = bxn - bxm;
-        dB[2] = sh.m[sc][3][si + 1] - sh.m[sc][3][si - 1];
-        dB[3] = byn - bym;
+        // undivided central differences a(+1) - a(-1) (scale 1/2 in kq)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const T ddx = rc[f * RS + si + 1] - rc[f * RS + si - 1];
+          const T ddy = rn[f * RS + si] - rs[f * RS + si];
+          if (f < 2) { dJ[2 * f] = ddx; dJ[2 * f + 1] = ddy; }
+          else { dB[2 * (f - 2)] = ddx; dB[2 * (f - 2) + 1] = ddy; }
+        }
       }
-      collide(p, rho1c, jxc, jyc, bxc, byc, dJ, dB, c);
-      T* o = dst + (size_t)y * pitch + x;
+      const T jx = rc[0 * RS + si], jy = rc[1 * RS + si], bx = rc[2 * RS + si], by = rc[3 * RS + si];
+      const T* st = S.stage[m % NST];
+      T p[kQ];
 #pragma unroll
-      for (int qq = 0; qq < kQ; ++qq) o[(size_t)qq * g.plane] = p[qq];
-      // rotate the row window
+      for (int q = 0; q < kQ; ++q) {
+        const int i = q % 9;
+        p[q] = st[group_of(i) * GE + (3 * (q / 9) + index_in_group(i)) * kBox + t + 4 - vel_x(i)];
+      }
+      collide(p, rho_cur, jx, jy, bx, by, dJ, dB, c);
+      const int y = row_of(m);
+      const int x = x0 + t;
+      T* o = dst + (size_t)y * pitch + kXOff + x;
 #pragma unroll
-      for (int qq = 0; qq < kQ; ++qq) p[qq] = q[qq];
-      jxm = jxc; jym = jyc; bxm = bxc; bym = byc;
-      rho1c = rho1n; jxc = jxn; jyc = jyn; bxc = bxn; byc = byn;
+      for (int q = 0; q < kQ; ++q) o[(size_t)plane_of(q) * g.plane] = p[q];
+      if (x < 2) {  // right ghosts: logical columns nx, nx + 1
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) o[(size_t)plane_of(q) * g.plane + nx] = p[q];
+      }
+      if (x >= nx - 2) {  // left ghosts: logical columns -2, -1
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) o[(size_t)plane_of(q) * g.plane - nx] = p[q];
+      }
     }
+    rho_cur = rho_next;
   }
 }
 
@@ -349,39 +349,68 @@ KCoef<T> cast_coef(const StepCoef& c) {
   return k;
 }
 
-template <typename T, int MINB>
-cudaError_t launch_step(const T* src, T* dst, const StepGeom& g, const StepCoef& c, int stencil,
-                        cudaStream_t s) {
+// Pipeline depth and residency per precision: binary32 rows are 15 KB per stage (4 stages,
+// 3 blocks per SM); binary64 rows are 30 KB (3 stages, 2 blocks per SM).
+template <typename T> struct StepConfig;
+template <> struct StepConfig<float> { static constexpr int kStages = 4, kMinBlocks = 3; };
+template <> struct StepConfig<double> { static constexpr int kStages = 3, kMinBlocks = 2; };
+
+template <typename T, int ISO>
+constexpr auto kernel_ptr() {
+  return &fused_step_kernel<T, ISO, StepConfig<T>::kStages, StepConfig<T>::kMinBlocks>;
+}
+
+template <typename T>
+constexpr size_t smem_bytes() {
+  return sizeof(StepSmem<T, StepConfig<T>::kStages>) + 128;  // + alignment slack
+}
+
+template <typename T>
+cudaError_t launch_step(const CUtensorMap& src, T* dst, const StepGeom& g, const StepCoef& c,
+                        int stencil, unsigned* err, cudaStream_t s) {
   dim3 grid((g.nx + kStepThreads - 1) / kStepThreads, (g.ny + g.band - 1) / g.band);
   KCoef<T> k = cast_coef<T>(c);
   if (stencil == 1)
-    fused_step_kernel<T, 1, MINB><<<grid, kStepThreads, 0, s>>>(src, dst, g, k);
+    kernel_ptr<T, 1>()<<<grid, kStepThreads, smem_bytes<T>(), s>>>(src, dst, g, k, err);
   else
-    fused_step_kernel<T, 0, MINB><<<grid, kStepThreads, 0, s>>>(src, dst, g, k);
+    kernel_ptr<T, 0>()<<<grid, kStepThreads, smem_bytes<T>(), s>>>(src, dst, g, k, err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_step_f64(const double* src, double* dst, const StepGeom& g, const StepCoef& c,
-                            int stencil, cudaStream_t s) {
-  return launch_step<double, 1>(src, dst, g, c, stencil, s);
+cudaError_t prepare_step_kernels() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(kernel_ptr<float, 0>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<float>())) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(kernel_ptr<float, 1>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<float>())) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(kernel_ptr<double, 0>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<double>())) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel_ptr<double, 1>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes<double>());
 }
 
-cudaError_t launch_step_f32(const float* src, float* dst, const StepGeom& g, const StepCoef& c,
-                            int stencil, cudaStream_t s) {
-  return launch_step<float, 3>(src, dst, g, c, stencil, s);
+cudaError_t launch_step_f64(const CUtensorMap& src, double* dst, const StepGeom& g,
+                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s) {
+  return launch_step<double>(src, dst, g, c, stencil, err, s);
 }
 
-// Rows per block: long bands amortise the two recomputed halo rows, short bands give enough
-// blocks to fill 152 SMs several times over.
+cudaError_t launch_step_f32(const CUtensorMap& src, float* dst, const StepGeom& g,
+                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s) {
+  return launch_step<float>(src, dst, g, c, stencil, err, s);
+}
+
+// Rows per block: with the blocks that fit on the GPU at once (`resident`), give every strip
+// floor(resident / strips) bands so the whole grid runs in one wave; never fewer than 4 rows.
 int step_band_rows(int nx, int ny, int precision, int num_sms) {
   const int strips = (nx + kStepThreads - 1) / kStepThreads;
-  const int per_sm = precision == 0 ? 1 : 3;  // resident blocks per SM (launch bounds)
-  const long target_blocks = (long)num_sms * per_sm * 4;  // about four waves
-  long band = ((long)strips * ny + target_blocks - 1) / target_blocks;
+  const int per_sm = precision == 0 ? StepConfig<double>::kMinBlocks : StepConfig<float>::kMinBlocks;
+  const long resident = (long)num_sms * per_sm;
+  long bands = resident / strips;
+  if (bands < 1) bands = 1;
+  long band = (ny + bands - 1) / bands;
   if (band < 4) band = 4;
-  if (band > 64) band = 64;
   if (band > ny) band = ny;
   return (int)band;
 }
