@@ -11,7 +11,7 @@
 // issues, per pulled row r, three 3-D box copies (cp.async.bulk.tensor) of 9 planes x kBox
 // columns each -- source rows r-1, r, r+1 of the three plane groups (planes are grouped by
 // c_y, see lbmhd_internal.cuh) -- completing on the row's mbarrier, NST-2 rows ahead of the
-// row being computed.  For row r the block then
+// row whose moments are being formed.  For row r the block then
 //   A. waits for row r+1, forms its moments (cell and the two halo columns) into a 4-row
 //      ring of J, B in shared memory;
 //   B. one CTA barrier; the elected thread refills the stage freed by row r-1;
@@ -349,11 +349,33 @@ KCoef<T> cast_coef(const StepCoef& c) {
   return k;
 }
 
-// Pipeline depth and residency per precision: binary32 rows are 15 KB per stage (4 stages,
-// 3 blocks per SM); binary64 rows are 30 KB (3 stages, 2 blocks per SM).
+// Pipeline depth and residency per precision.  binary32 rows are 15 KB per stage: 3 stages
+// (one row in flight) and 4 blocks per SM (16 warps, 128 registers) measured fastest at 2048^2
+// and 4096^2 -- more resident warps beat deeper pipelines (4 stages x 3 blocks: 0.81 of the
+// copy bandwidth, 3 x 4: 0.92).  binary64 rows are 30 KB: 3 stages, 2 blocks per SM; that
+// form is bound by the binary64 arithmetic rate.  Overridable at build time for sweeps.
+#ifndef LBMHD_F32_STAGES
+#define LBMHD_F32_STAGES 3
+#endif
+#ifndef LBMHD_F32_BLOCKS
+#define LBMHD_F32_BLOCKS 4
+#endif
+#ifndef LBMHD_F64_STAGES
+#define LBMHD_F64_STAGES 3
+#endif
+#ifndef LBMHD_F64_BLOCKS
+#define LBMHD_F64_BLOCKS 2
+#endif
+#ifndef LBMHD_WAVES
+#define LBMHD_WAVES 1
+#endif
 template <typename T> struct StepConfig;
-template <> struct StepConfig<float> { static constexpr int kStages = 4, kMinBlocks = 3; };
-template <> struct StepConfig<double> { static constexpr int kStages = 3, kMinBlocks = 2; };
+template <> struct StepConfig<float> {
+  static constexpr int kStages = LBMHD_F32_STAGES, kMinBlocks = LBMHD_F32_BLOCKS;
+};
+template <> struct StepConfig<double> {
+  static constexpr int kStages = LBMHD_F64_STAGES, kMinBlocks = LBMHD_F64_BLOCKS;
+};
 
 template <typename T, int ISO>
 constexpr auto kernel_ptr() {
@@ -406,7 +428,7 @@ cudaError_t launch_step_f32(const CUtensorMap& src, float* dst, const StepGeom& 
 int step_band_rows(int nx, int ny, int precision, int num_sms) {
   const int strips = (nx + kStepThreads - 1) / kStepThreads;
   const int per_sm = precision == 0 ? StepConfig<double>::kMinBlocks : StepConfig<float>::kMinBlocks;
-  const long resident = (long)num_sms * per_sm;
+  const long resident = (long)num_sms * per_sm * LBMHD_WAVES;
   long bands = resident / strips;
   if (bands < 1) bands = 1;
   long band = (ny + bands - 1) / bands;
