@@ -1,0 +1,65 @@
+"""Multi-rank host logic of bench.py on CPU (gloo, world size 2): every rank runs its own
+replica, so the only cross-rank operations are the barrier and the max over ranks of the
+timed interval; rank 0 alone prints.  The reference arm runs on rank 0 only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update({"RANK": str(rank), "LOCAL_RANK": str(rank), "WORLD_SIZE": str(world),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    sys.path.insert(0, ROOT)
+    import bench
+    import torch.distributed as dist
+    r, ws, local = bench.dist_setup()
+    assert (r, ws, local) == (rank, world, rank)
+    assert dist.get_backend() == "gloo"
+    bench.barrier(ws)
+    m = bench.max_over_ranks(10.0 + rank, ws)
+    q.put((rank, m))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_barrier_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=5) for _ in range(2))
+    assert got == [(0, 11.0), (1, 11.0)]
+
+
+def test_reference_arm_runs_on_rank0_only(tmp_path):
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "3", "--warmup", "1"], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_single_process_defaults():
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.pop("WORLD_SIZE", None)
+    assert bench.dist_setup() == (0, 1, 0)
+    assert bench.max_over_ranks(3.5, 1) == 3.5
+    assert bench.workload_name(2048, "fp32", 0.0) == "kh_jet_2048x2048_dns_fp32"
+    assert bench.workload_name(256, "fp32", 2.0) == "kh_jet_256x256_les_delta2_fp32"
