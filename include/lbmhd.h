@@ -46,6 +46,7 @@ extern "C" {
 /* Storage / arithmetic forms of the populations. */
 #define LBMHD_FP64 0 /* populations stored in binary64, collision in binary64 */
 #define LBMHD_FP32 1 /* f_i - w_i and g_i stored in binary32, collision in binary32 */
+#define LBMHD_FP16 2 /* f_i - w_i and g_i stored in binary16, collision in binary32 */
 
 /* Finite-difference stencils for d_beta (the paper leaves the discretisation open). */
 #define LBMHD_GRAD_CENTRAL 0   /* (a(x+e_beta) - a(x-e_beta)) / 2 */
@@ -66,7 +67,7 @@ typedef struct {
   double s_m;        /* magnetic SRT rate (Eq. LBMagEqn), in (0, 2); eta = 1/(3 s_m) - 1/6 */
   double delta;      /* filter width Delta in lattice units, >= 0; the Delta^2/12 terms of
                         Sec. 2.1; 0 gives plain (DNS) LB-MHD */
-  int precision;     /* LBMHD_FP64 or LBMHD_FP32 */
+  int precision;     /* LBMHD_FP64, LBMHD_FP32 or LBMHD_FP16 */
   int grad_stencil;  /* LBMHD_GRAD_CENTRAL or LBMHD_GRAD_ISOTROPIC */
   void* cuda_stream; /* cudaStream_t to run on; NULL: the handle creates its own stream */
 } lbmhd_params;
@@ -102,7 +103,7 @@ int lbmhd_moments_device(lbmhd_t* h, double* rho, double* ux, double* uy, double
                          double* by);
 
 /* Current populations in canonical layout [27][ny][nx] (binary64), host array of
- * 27*nx*ny doubles; synchronises.  For FP32 handles the stored values are widened. */
+ * 27*nx*ny doubles; synchronises.  For FP32 / FP16 handles the stored values are widened. */
 int lbmhd_get_populations(lbmhd_t* h, double* pops);
 
 /* Double-precision diagnostics of the current state (host array of LBMHD_NDIAG):

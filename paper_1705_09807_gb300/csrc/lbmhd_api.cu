@@ -91,7 +91,7 @@ int check_params(const lbmhd_params* p) {
     return fail(nullptr, LBMHD_ERR_INVALID, "s_m = %g outside (0, 2)", p->s_m);
   if (!(p->delta >= 0.0) || !std::isfinite(p->delta))
     return fail(nullptr, LBMHD_ERR_INVALID, "delta = %g must be finite and >= 0", p->delta);
-  if (p->precision != LBMHD_FP64 && p->precision != LBMHD_FP32)
+  if (p->precision != LBMHD_FP64 && p->precision != LBMHD_FP32 && p->precision != LBMHD_FP16)
     return fail(nullptr, LBMHD_ERR_INVALID, "unknown precision %d", p->precision);
   if (p->grad_stencil != LBMHD_GRAD_CENTRAL && p->grad_stencil != LBMHD_GRAD_ISOTROPIC)
     return fail(nullptr, LBMHD_ERR_INVALID, "unknown grad_stencil %d", p->grad_stencil);
@@ -145,17 +145,20 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 3-D map {pitch, ny, 27} over one population copy, boxes of {kBox, 1, 9} (one row of one
-// 9-plane group, the strip plus 4 columns each side).
+// 3-D map {pitch, ny, 27} over one population copy, boxes of {box_width, 1, 9} (one row of one
+// 9-plane group: the strip plus box_lead columns on each side).
 int make_tensor_map(lbmhd_t* h, void* base, CUtensorMap* map) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return fail(nullptr, LBMHD_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   const cuuint64_t e = h->elem;
   cuuint64_t dims[3] = {(cuuint64_t)h->geom.pitch, (cuuint64_t)h->geom.ny, (cuuint64_t)kQ};
   cuuint64_t strides[2] = {(cuuint64_t)h->geom.pitch * e, (cuuint64_t)h->geom.plane * e};
-  cuuint32_t box[3] = {(cuuint32_t)kBox, 1, 9};
+  cuuint32_t box[3] = {(cuuint32_t)box_width((int)e), 1, 9};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(map, e == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+  const CUtensorMapDataType dt = e == 8   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : e == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUresult r = enc(map, dt, 3,
                    base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -181,7 +184,7 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
   if (!h) return fail(nullptr, LBMHD_ERR_OOM, "host allocation failed");
   h->p = *p;
   h->precision = p->precision;
-  h->elem = p->precision == LBMHD_FP64 ? 8 : 4;
+  h->elem = p->precision == LBMHD_FP64 ? 8 : (p->precision == LBMHD_FP32 ? 4 : 2);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) {
     delete h;
@@ -242,6 +245,21 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
   return LBMHD_OK;
 }
 
+// One fused step from copy `from` into copy `to`.
+cudaError_t launch_one(lbmhd_t* h, int from, int to) {
+  switch (h->precision) {
+    case LBMHD_FP64:
+      return launch_step_f64(h->tmap[from], (double*)h->pops[to], h->geom, h->coef,
+                             h->p.grad_stencil, h->err_flag, h->stream);
+    case LBMHD_FP32:
+      return launch_step_f32(h->tmap[from], (float*)h->pops[to], h->geom, h->coef,
+                             h->p.grad_stencil, h->err_flag, h->stream);
+    default:
+      return launch_step_f16(h->tmap[from], (__half*)h->pops[to], h->geom, h->coef,
+                             h->p.grad_stencil, h->err_flag, h->stream);
+  }
+}
+
 int build_graph(lbmhd_t* h, int parity) {
   cudaGraph_t graph = nullptr;
   LB_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -249,12 +267,7 @@ int build_graph(lbmhd_t* h, int parity) {
   cudaError_t le = cudaSuccess;
   for (int n = 0; n < kGraphSteps && le == cudaSuccess; ++n) {
     const int nxt = cur ^ 1;
-    if (h->precision == LBMHD_FP64)
-      le = launch_step_f64(h->tmap[cur], (double*)h->pops[nxt], h->geom, h->coef,
-                           h->p.grad_stencil, h->err_flag, h->stream);
-    else
-      le = launch_step_f32(h->tmap[cur], (float*)h->pops[nxt], h->geom, h->coef,
-                           h->p.grad_stencil, h->err_flag, h->stream);
+    le = launch_one(h, cur, nxt);
     cur = nxt;
   }
   cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
@@ -275,12 +288,7 @@ int build_graph(lbmhd_t* h, int parity) {
 int one_step(lbmhd_t* h) {
   const int nxt = h->cur ^ 1;
   cudaError_t e;
-  if (h->precision == LBMHD_FP64)
-    e = launch_step_f64(h->tmap[h->cur], (double*)h->pops[nxt], h->geom, h->coef,
-                        h->p.grad_stencil, h->err_flag, h->stream);
-  else
-    e = launch_step_f32(h->tmap[h->cur], (float*)h->pops[nxt], h->geom, h->coef,
-                        h->p.grad_stencil, h->err_flag, h->stream);
+  e = launch_one(h, h->cur, nxt);
   if (e != cudaSuccess) return cuda_fail(h, e, "fused step launch");
   h->cur = nxt;
   h->launches += 1;

@@ -34,7 +34,7 @@ __global__ void init_eq_kernel(T* __restrict__ pops, StepGeom g, const double* _
       const double gx = w * (b + 3.0 * (cu * b - cb * u));
       const double gy = w * (d + 3.0 * (cu * d - cb * v));
       const size_t o = (size_t)y * g.pitch + kXOff + x;
-      const T vals[3] = {(T)fdev, (T)gx, (T)gy};
+      const T vals[3] = {store_as<T>(fdev), store_as<T>(gx), store_as<T>(gy)};
 #pragma unroll
       for (int comp = 0; comp < 3; ++comp) {
         T* pl = pops + (size_t)plane_of(9 * comp + i) * g.plane + o;
@@ -54,7 +54,7 @@ __device__ __forceinline__ void pull_cell(const T* __restrict__ pops, const Step
   for (int q = 0; q < 27; ++q) {
     const int i = q % 9;
     const int sx = wrapi(x - vx(i), g.nx), sy = wrapi(y - vy(i), g.ny);
-    v[q] = (double)pops[(size_t)plane_of(q) * g.plane + (size_t)sy * g.pitch + kXOff + sx];
+    v[q] = load_as<double>(pops[(size_t)plane_of(q) * g.plane + (size_t)sy * g.pitch + kXOff + sx]);
   }
 }
 
@@ -191,8 +191,10 @@ cudaError_t launch_init_eq(int precision, void* pops, const StepGeom& g, const d
   const int grid = grid_for((long)g.nx * g.ny, 256);
   if (precision == 0)
     init_eq_kernel<double><<<grid, 256, 0, s>>>((double*)pops, g, rho, ux, uy, bx, by);
-  else
+  else if (precision == 1)
     init_eq_kernel<float><<<grid, 256, 0, s>>>((float*)pops, g, rho, ux, uy, bx, by);
+  else
+    init_eq_kernel<__half><<<grid, 256, 0, s>>>((__half*)pops, g, rho, ux, uy, bx, by);
   return cudaGetLastError();
 }
 
@@ -201,8 +203,10 @@ cudaError_t launch_moments(int precision, const void* pops, const StepGeom& g, d
   const int grid = grid_for((long)g.nx * g.ny, 256);
   if (precision == 0)
     moments_kernel<double><<<grid, 256, 0, s>>>((const double*)pops, g, rho, ux, uy, bx, by);
-  else
+  else if (precision == 1)
     moments_kernel<float><<<grid, 256, 0, s>>>((const float*)pops, g, rho, ux, uy, bx, by);
+  else
+    moments_kernel<__half><<<grid, 256, 0, s>>>((const __half*)pops, g, rho, ux, uy, bx, by);
   return cudaGetLastError();
 }
 
@@ -211,8 +215,10 @@ cudaError_t launch_populations(int precision, const void* pops, const StepGeom& 
   const int grid = grid_for((long)g.nx * g.ny, 256);
   if (precision == 0)
     populations_kernel<double><<<grid, 256, 0, s>>>((const double*)pops, g, out);
-  else
+  else if (precision == 1)
     populations_kernel<float><<<grid, 256, 0, s>>>((const float*)pops, g, out);
+  else
+    populations_kernel<__half><<<grid, 256, 0, s>>>((const __half*)pops, g, out);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -29,7 +30,12 @@ constexpr int kQ = 27;             // populations per cell: 9 (f) + 2 x 9 (g)
 constexpr int kStepThreads = 128;  // threads (= columns) per block of the fused step
 constexpr int kRing = 4;           // rows of moments kept in shared memory
 constexpr int kXOff = 32;          // physical column of logical x = 0
-constexpr int kBox = kStepThreads + 8;  // columns per staged row segment: strip +- 4
+// Staged row segment of a strip: it starts `box_lead` columns left of the strip (so its first
+// byte is 16-byte aligned for the tensor copy) and spans the strip plus a lead on each side.
+__host__ __device__ constexpr int box_lead(int elem_bytes) { return elem_bytes == 2 ? 8 : 4; }
+__host__ __device__ constexpr int box_width(int elem_bytes) {
+  return kStepThreads + 2 * box_lead(elem_bytes);
+}
 
 // Paper's D2Q9 velocity order (Sec. 2): c_x = {0,1,0,-1,0,1,-1,-1,1}, c_y = {0,0,1,0,-1,1,1,-1,-1}.
 __host__ __device__ constexpr int vel_x(int i) {
@@ -51,6 +57,20 @@ __host__ __device__ constexpr double lattice_w(int i) {
   return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
+// Conversions between the storage type S of the populations and the arithmetic type C.
+template <typename C, typename S>
+__device__ __forceinline__ C load_as(S v) { return static_cast<C>(v); }
+template <>
+__device__ __forceinline__ float load_as<float, __half>(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ double load_as<double, __half>(__half v) { return (double)__half2float(v); }
+template <typename S, typename C>
+__device__ __forceinline__ S store_as(C v) { return static_cast<S>(v); }
+template <>
+__device__ __forceinline__ __half store_as<__half, float>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __half store_as<__half, double>(double v) { return __double2half(v); }
+
 // Per-launch constants of the fused step, computed on the host in binary64.
 struct StepCoef {
   double r[9];   // r[j] = s_j / |T_j|^2 for j = 3..8 (relaxation scaled by T T^T's diagonal)
@@ -65,18 +85,20 @@ struct StepGeom {
 };
 
 // Fused step launchers (lbmhd_step.cu).  `src` is a 3-D tensor map {pitch, ny, 27} of the
-// source copy (box {kBox, 1, 9}); dst is the other copy.  *err receives 1 if a pipeline wait
+// source copy (box {box_width(elem), 1, 9}); dst is the other copy.  *err receives 1 if a pipeline wait
 // timed out (the kernel then stops early; the state is not valid).
 cudaError_t launch_step_f64(const CUtensorMap& src, double* dst, const StepGeom& g,
                             const StepCoef& c, int stencil, unsigned* err, cudaStream_t s);
 cudaError_t launch_step_f32(const CUtensorMap& src, float* dst, const StepGeom& g,
+                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s);
+cudaError_t launch_step_f16(const CUtensorMap& src, __half* dst, const StepGeom& g,
                             const StepCoef& c, int stencil, unsigned* err, cudaStream_t s);
 // Rows per block for the grid and precision (one wave of resident blocks when possible).
 int step_band_rows(int nx, int ny, int precision, int num_sms);
 // Opt the step kernels in to their dynamic shared memory (once per process and device).
 cudaError_t prepare_step_kernels();
 
-// Auxiliary kernels (lbmhd_aux.cu).  `precision` selects double / float storage.
+// Auxiliary kernels (lbmhd_aux.cu).  `precision` selects double / float / half storage.
 cudaError_t launch_init_eq(int precision, void* pops, const StepGeom& g, const double* rho,
                            const double* ux, const double* uy, const double* bx, const double* by,
                            cudaStream_t s);

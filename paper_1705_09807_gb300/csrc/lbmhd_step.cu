@@ -8,7 +8,7 @@
 // band row by row (adjacent bands march in opposite directions, so the two rows a band shares
 // with its neighbour are fetched by both at about the same time and the second fetch hits L2).
 // Rows are staged in shared memory by the tensor-memory accelerator: one elected thread
-// issues, per pulled row r, three 3-D box copies (cp.async.bulk.tensor) of 9 planes x kBox
+// issues, per pulled row r, three 3-D box copies (cp.async.bulk.tensor) of 9 planes x the strip
 // columns each -- source rows r-1, r, r+1 of the three plane groups (planes are grouped by
 // c_y, see lbmhd_internal.cuh) -- completing on the row's mbarrier, NST-2 rows ahead of the
 // row whose moments are being formed.  For row r the block then
@@ -139,27 +139,37 @@ __device__ __forceinline__ void collide(T p[kQ], T rho1, T jx, T jy, T bx, T by,
 }
 
 
+// Arithmetic type for each storage type: binary16 populations are collided in binary32.
+template <typename S> struct ArithOf { using type = S; };
+template <> struct ArithOf<__half> { using type = float; };
+
 // Shared memory of one block: NST row stages, the moment ring, the stage barriers.
-template <typename T, int NST>
+template <typename S, int NST>
 struct StepSmem {
-  static constexpr int kGroupElems = ((9 * kBox * (int)sizeof(T) + 127) / 128 * 128) / (int)sizeof(T);
+  using C = typename ArithOf<S>::type;
+  static constexpr int kLead = box_lead((int)sizeof(S));
+  static constexpr int kBoxW = box_width((int)sizeof(S));
+  static constexpr int kGroupElems = ((9 * kBoxW * (int)sizeof(S) + 127) / 128 * 128) / (int)sizeof(S);
   static constexpr int kStageElems = 3 * kGroupElems;
-  static constexpr uint32_t kTxBytes = 3u * 9u * kBox * sizeof(T);  // bytes landing per stage
-  T stage[NST][kStageElems];
-  T ring[kRing][4][kStepThreads + 2];
+  static constexpr uint32_t kTxBytes = 3u * 9u * kBoxW * sizeof(S);  // bytes landing per stage
+  S stage[NST][kStageElems];
+  C ring[kRing][4][kStepThreads + 2];
   uint64_t full[NST];
   int abort_flag[2];
 };
 
-template <typename T>
-__device__ __forceinline__ void moments_from(const T* st, int ge, int col, T& rho1, T& jx, T& jy,
-                                             T& bx, T& by) {
-  // pulled population (i, comp) of the cell at box column `col`
-  auto v = [&](int q) -> T {
-    const int i = q % 9;
-    return st[group_of(i) * ge + (3 * (q / 9) + index_in_group(i)) * kBox + col - vel_x(i)];
-  };
-  const T f0 = v(0), f1 = v(1), f2 = v(2), f3 = v(3), f4 = v(4), f5 = v(5), f6 = v(6), f7 = v(7),
+// Pulled population q of the cell at box column `col` of a staged row.
+template <typename C, typename S, int BW>
+__device__ __forceinline__ C staged(const S* st, int ge, int q, int col) {
+  const int i = q % 9;
+  return load_as<C>(st[group_of(i) * ge + (3 * (q / 9) + index_in_group(i)) * BW + col - vel_x(i)]);
+}
+
+template <typename C, typename S, int BW>
+__device__ __forceinline__ void moments_from(const S* st, int ge, int col, C& rho1, C& jx, C& jy,
+                                             C& bx, C& by) {
+  auto v = [&](int q) -> C { return staged<C, S, BW>(st, ge, q, col); };
+  const C f0 = v(0), f1 = v(1), f2 = v(2), f3 = v(3), f4 = v(4), f5 = v(5), f6 = v(6), f7 = v(7),
           f8 = v(8);
   rho1 = ((f0 + f1) + (f2 + f3)) + ((f4 + f5) + (f6 + f7)) + f8;
   jx = (f1 - f3) + (f5 - f6) + (f8 - f7);
@@ -168,15 +178,18 @@ __device__ __forceinline__ void moments_from(const T* st, int ge, int col, T& rh
   by = ((v(18) + v(19)) + (v(20) + v(21))) + ((v(22) + v(23)) + (v(24) + v(25))) + v(26);
 }
 
-template <typename T, int ISO, int NST, int MINB>
+template <typename S, int ISO, int NST, int MINB>
 __global__ void __launch_bounds__(kStepThreads, MINB)
-    fused_step_kernel(const __grid_constant__ CUtensorMap src, T* __restrict__ dst, StepGeom g,
-                      KCoef<T> c, unsigned* __restrict__ err) {
-  using SM = StepSmem<T, NST>;
+    fused_step_kernel(const __grid_constant__ CUtensorMap src, S* __restrict__ dst, StepGeom g,
+                      KCoef<typename ArithOf<S>::type> c, unsigned* __restrict__ err) {
+  using SM = StepSmem<S, NST>;
+  using T = typename SM::C;
+  constexpr int GE = SM::kGroupElems;
+  constexpr int LEAD = SM::kLead;
+  constexpr int BW = SM::kBoxW;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // TMA destinations need 128-byte alignment: round the dynamic base up (slack reserved)
-  SM& S = *reinterpret_cast<SM*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
-  constexpr int GE = SM::kGroupElems;
+  SM& S_ = *reinterpret_cast<SM*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
 
   const int t = threadIdx.x;
   const int nx = g.nx, ny = g.ny;
@@ -200,24 +213,24 @@ __global__ void __launch_bounds__(kStepThreads, MINB)
     const int r = row_of(k);
     const int ra = r == 0 ? ny - 1 : r - 1;  // c_y = +1 group is pulled from row r - 1
     const int rc = r == ny - 1 ? 0 : r + 1;  // c_y = -1 group from row r + 1
-    const int cx = x0 + kXOff - 4;           // box covers logical columns x0-4 .. x0+kBox-5
-    mbar_arrive_expect_tx(&S.full[s], SM::kTxBytes);
-    tma_load_3d(&S.stage[s][0], &src, cx, ra, 0, &S.full[s]);
-    tma_load_3d(&S.stage[s][GE], &src, cx, r, 9, &S.full[s]);
-    tma_load_3d(&S.stage[s][2 * GE], &src, cx, rc, 18, &S.full[s]);
+    const int cx = x0 + kXOff - LEAD;        // box covers logical columns x0-LEAD .. x0+BW-LEAD-1
+    mbar_arrive_expect_tx(&S_.full[s], SM::kTxBytes);
+    tma_load_3d(&S_.stage[s][0], &src, cx, ra, 0, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][GE], &src, cx, r, 9, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][2 * GE], &src, cx, rc, 18, &S_.full[s]);
   };
   auto wait_row = [&](int k) -> bool {
-    return mbar_wait_bounded(&S.full[k % NST], (uint32_t)((k / NST) & 1), kWaitLimitNs);
+    return mbar_wait_bounded(&S_.full[k % NST], (uint32_t)((k / NST) & 1), kWaitLimitNs);
   };
   // moments of staged row k into ring slot k & 3 (own column and the strip's halo columns)
   T rho_next = T(0);
   auto ring_moments = [&](int k) {
-    const T* st = S.stage[k % NST];
-    T* rg = &S.ring[k & (kRing - 1)][0][0];
+    const S* st = S_.stage[k % NST];
+    T* rg = &S_.ring[k & (kRing - 1)][0][0];
     constexpr int RS = kStepThreads + 2;
     T r1, jx, jy, bx, by;
     if (active) {
-      moments_from(st, GE, t + 4, r1, jx, jy, bx, by);
+      moments_from<T, S, BW>(st, GE, t + LEAD, r1, jx, jy, bx, by);
       rg[0 * RS + t + 1] = jx;
       rg[1 * RS + t + 1] = jy;
       rg[2 * RS + t + 1] = bx;
@@ -225,14 +238,14 @@ __global__ void __launch_bounds__(kStepThreads, MINB)
       rho_next = r1;
     }
     if (t == 0) {  // column x0 - 1
-      moments_from(st, GE, 3, r1, jx, jy, bx, by);
+      moments_from<T, S, BW>(st, GE, LEAD - 1, r1, jx, jy, bx, by);
       rg[0 * RS] = jx;
       rg[1 * RS] = jy;
       rg[2 * RS] = bx;
       rg[3 * RS] = by;
     }
     if (t == ncol - 1) {  // column x0 + ncol
-      moments_from(st, GE, ncol + 4, r1, jx, jy, bx, by);
+      moments_from<T, S, BW>(st, GE, ncol + LEAD, r1, jx, jy, bx, by);
       rg[0 * RS + ncol + 1] = jx;
       rg[1 * RS + ncol + 1] = jy;
       rg[2 * RS + ncol + 1] = bx;
@@ -241,9 +254,9 @@ __global__ void __launch_bounds__(kStepThreads, MINB)
   };
 
   if (t == 0) {
-    for (int s = 0; s < NST; ++s) mbar_init(&S.full[s], 1);
-    S.abort_flag[0] = 0;
-    S.abort_flag[1] = 0;
+    for (int s = 0; s < NST; ++s) mbar_init(&S_.full[s], 1);
+    S_.abort_flag[0] = 0;
+    S_.abort_flag[1] = 0;
     fence_barrier_init();
     prefetch_tmap(&src);
   }
@@ -254,17 +267,17 @@ __global__ void __launch_bounds__(kStepThreads, MINB)
   int issued = first;  // meaningful in thread 0 only
 
   // prologue: rows k = 0 and k = 1
-  if (wait_row(0)) ring_moments(0); else S.abort_flag[1] = 1;
-  if (wait_row(1)) ring_moments(1); else S.abort_flag[1] = 1;
+  if (wait_row(0)) ring_moments(0); else S_.abort_flag[1] = 1;
+  if (wait_row(1)) ring_moments(1); else S_.abort_flag[1] = 1;
   T rho_cur = rho_next;
 
   const size_t pitch = (size_t)g.pitch;
   for (int m = 1; m <= L - 2; ++m) {
     // A: moments of the next row
-    if (wait_row(m + 1)) ring_moments(m + 1); else S.abort_flag[m & 1] = 1;
+    if (wait_row(m + 1)) ring_moments(m + 1); else S_.abort_flag[m & 1] = 1;
     // B
     __syncthreads();
-    if (S.abort_flag[m & 1]) {
+    if (S_.abort_flag[m & 1]) {
       if (t == 0) {
         atomicOr(err, 1u);
         for (int k = m + 1; k < issued; ++k) wait_row(k);  // drain copies still in flight
@@ -279,9 +292,9 @@ __global__ void __launch_bounds__(kStepThreads, MINB)
     // C: gradients, collision and store of row m
     if (active) {
       constexpr int RS = kStepThreads + 2;
-      const T* rc = &S.ring[m & (kRing - 1)][0][0];
-      const T* rn = &S.ring[(dir > 0 ? m + 1 : m - 1) & (kRing - 1)][0][0];  // row y + 1
-      const T* rs = &S.ring[(dir > 0 ? m - 1 : m + 1) & (kRing - 1)][0][0];  // row y - 1
+      const T* rc = &S_.ring[m & (kRing - 1)][0][0];
+      const T* rn = &S_.ring[(dir > 0 ? m + 1 : m - 1) & (kRing - 1)][0][0];  // row y + 1
+      const T* rs = &S_.ring[(dir > 0 ? m - 1 : m + 1) & (kRing - 1)][0][0];  // row y - 1
       const int si = t + 1;
       T dJ[4], dB[4];
       if (ISO) {
@@ -309,26 +322,23 @@ __global__ void __launch_bounds__(kStepThreads, MINB)
         }
       }
       const T jx = rc[0 * RS + si], jy = rc[1 * RS + si], bx = rc[2 * RS + si], by = rc[3 * RS + si];
-      const T* st = S.stage[m % NST];
+      const S* st = S_.stage[m % NST];
       T p[kQ];
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) {
-        const int i = q % 9;
-        p[q] = st[group_of(i) * GE + (3 * (q / 9) + index_in_group(i)) * kBox + t + 4 - vel_x(i)];
-      }
+      for (int q = 0; q < kQ; ++q) p[q] = staged<T, S, BW>(st, GE, q, t + LEAD);
       collide(p, rho_cur, jx, jy, bx, by, dJ, dB, c);
       const int y = row_of(m);
       const int x = x0 + t;
-      T* o = dst + (size_t)y * pitch + kXOff + x;
+      S* o = dst + (size_t)y * pitch + kXOff + x;
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) o[(size_t)plane_of(q) * g.plane] = p[q];
+      for (int q = 0; q < kQ; ++q) o[(size_t)plane_of(q) * g.plane] = store_as<S>(p[q]);
       if (x < 2) {  // right ghosts: logical columns nx, nx + 1
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) o[(size_t)plane_of(q) * g.plane + nx] = p[q];
+        for (int q = 0; q < kQ; ++q) o[(size_t)plane_of(q) * g.plane + nx] = store_as<S>(p[q]);
       }
       if (x >= nx - 2) {  // left ghosts: logical columns -2, -1
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) o[(size_t)plane_of(q) * g.plane - nx] = p[q];
+        for (int q = 0; q < kQ; ++q) o[(size_t)plane_of(q) * g.plane - nx] = store_as<S>(p[q]);
       }
     }
     rho_cur = rho_next;
@@ -349,11 +359,13 @@ KCoef<T> cast_coef(const StepCoef& c) {
   return k;
 }
 
-// Pipeline depth and residency per precision.  binary32 rows are 15 KB per stage: 3 stages
+// Pipeline depth and residency per storage type.  binary32 rows are 15 KB per stage: 3 stages
 // (one row in flight) and 4 blocks per SM (16 warps, 128 registers) measured fastest at 2048^2
 // and 4096^2 -- more resident warps beat deeper pipelines (4 stages x 3 blocks: 0.81 of the
-// copy bandwidth, 3 x 4: 0.92).  binary64 rows are 30 KB: 3 stages, 2 blocks per SM; that
-// form is bound by the binary64 arithmetic rate.  Overridable at build time for sweeps.
+// copy bandwidth, 3 x 4: 0.92).  binary16 rows are 8 KB and that form is bound by instruction
+// issue rather than memory (about 40 GLUPS for any depth/residency tried); 3 stages x 6 blocks
+// (76 registers) measured best.  binary64 rows are 30 KB: 3 stages, 2 blocks per SM; that form
+// is bound by the binary64 arithmetic rate.  Overridable at build time for sweeps.
 #ifndef LBMHD_F32_STAGES
 #define LBMHD_F32_STAGES 3
 #endif
@@ -369,48 +381,61 @@ KCoef<T> cast_coef(const StepCoef& c) {
 #ifndef LBMHD_WAVES
 #define LBMHD_WAVES 1
 #endif
-template <typename T> struct StepConfig;
+#ifndef LBMHD_F16_STAGES
+#define LBMHD_F16_STAGES 3
+#endif
+#ifndef LBMHD_F16_BLOCKS
+#define LBMHD_F16_BLOCKS 6
+#endif
+template <typename S> struct StepConfig;
 template <> struct StepConfig<float> {
   static constexpr int kStages = LBMHD_F32_STAGES, kMinBlocks = LBMHD_F32_BLOCKS;
 };
 template <> struct StepConfig<double> {
   static constexpr int kStages = LBMHD_F64_STAGES, kMinBlocks = LBMHD_F64_BLOCKS;
 };
+template <> struct StepConfig<__half> {
+  static constexpr int kStages = LBMHD_F16_STAGES, kMinBlocks = LBMHD_F16_BLOCKS;
+};
 
-template <typename T, int ISO>
+template <typename S, int ISO>
 constexpr auto kernel_ptr() {
-  return &fused_step_kernel<T, ISO, StepConfig<T>::kStages, StepConfig<T>::kMinBlocks>;
+  return &fused_step_kernel<S, ISO, StepConfig<S>::kStages, StepConfig<S>::kMinBlocks>;
 }
 
-template <typename T>
+template <typename S>
 constexpr size_t smem_bytes() {
-  return sizeof(StepSmem<T, StepConfig<T>::kStages>) + 128;  // + alignment slack
+  return sizeof(StepSmem<S, StepConfig<S>::kStages>) + 128;  // + alignment slack
 }
 
-template <typename T>
-cudaError_t launch_step(const CUtensorMap& src, T* dst, const StepGeom& g, const StepCoef& c,
+template <typename S>
+cudaError_t launch_step(const CUtensorMap& src, S* dst, const StepGeom& g, const StepCoef& c,
                         int stencil, unsigned* err, cudaStream_t s) {
   dim3 grid((g.nx + kStepThreads - 1) / kStepThreads, (g.ny + g.band - 1) / g.band);
-  KCoef<T> k = cast_coef<T>(c);
+  auto k = cast_coef<typename ArithOf<S>::type>(c);
   if (stencil == 1)
-    kernel_ptr<T, 1>()<<<grid, kStepThreads, smem_bytes<T>(), s>>>(src, dst, g, k, err);
+    kernel_ptr<S, 1>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(src, dst, g, k, err);
   else
-    kernel_ptr<T, 0>()<<<grid, kStepThreads, smem_bytes<T>(), s>>>(src, dst, g, k, err);
+    kernel_ptr<S, 0>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(src, dst, g, k, err);
   return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t set_smem_attr() {
+  cudaError_t e = cudaFuncSetAttribute(kernel_ptr<S, 0>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<S>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel_ptr<S, 1>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes<S>());
 }
 
 }  // namespace
 
 cudaError_t prepare_step_kernels() {
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(kernel_ptr<float, 0>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes<float>())) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(kernel_ptr<float, 1>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes<float>())) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(kernel_ptr<double, 0>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes<double>())) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kernel_ptr<double, 1>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_bytes<double>());
+  cudaError_t e = set_smem_attr<float>();
+  if (e == cudaSuccess) e = set_smem_attr<double>();
+  if (e == cudaSuccess) e = set_smem_attr<__half>();
+  return e;
 }
 
 cudaError_t launch_step_f64(const CUtensorMap& src, double* dst, const StepGeom& g,
@@ -423,11 +448,18 @@ cudaError_t launch_step_f32(const CUtensorMap& src, float* dst, const StepGeom& 
   return launch_step<float>(src, dst, g, c, stencil, err, s);
 }
 
+cudaError_t launch_step_f16(const CUtensorMap& src, __half* dst, const StepGeom& g,
+                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s) {
+  return launch_step<__half>(src, dst, g, c, stencil, err, s);
+}
+
 // Rows per block: with the blocks that fit on the GPU at once (`resident`), give every strip
 // floor(resident / strips) bands so the whole grid runs in one wave; never fewer than 4 rows.
 int step_band_rows(int nx, int ny, int precision, int num_sms) {
   const int strips = (nx + kStepThreads - 1) / kStepThreads;
-  const int per_sm = precision == 0 ? StepConfig<double>::kMinBlocks : StepConfig<float>::kMinBlocks;
+  const int per_sm = precision == 0   ? StepConfig<double>::kMinBlocks
+                     : precision == 1 ? StepConfig<float>::kMinBlocks
+                                      : StepConfig<__half>::kMinBlocks;
   const long resident = (long)num_sms * per_sm * LBMHD_WAVES;
   long bands = resident / strips;
   if (bands < 1) bands = 1;

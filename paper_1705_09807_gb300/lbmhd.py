@@ -25,6 +25,8 @@ LBMHD_ERR_OOM = -3
 LBMHD_ERR_UNSTABLE = -4
 LBMHD_FP64 = 0
 LBMHD_FP32 = 1
+LBMHD_FP16 = 2
+LBMHD_ERR_TIMEOUT = -5
 LBMHD_GRAD_CENTRAL = 0
 LBMHD_GRAD_ISOTROPIC = 1
 LBMHD_NDIAG = 10

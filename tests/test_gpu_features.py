@@ -25,7 +25,7 @@ def _params(n, precision=lbmhd.LBMHD_FP64, delta=2.0, stream=None, stencil=0):
     return lbmhd.make_params(n, n, s, sm, delta, precision, stencil, stream)
 
 
-@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32])
+@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32, lbmhd.LBMHD_FP16])
 def test_checkpoint_resume_bitwise(precision):
     fields = kh_jet(96, seed=4)
     with lbmhd.Lbmhd(_params(96, precision), *fields) as sim:

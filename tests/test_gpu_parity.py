@@ -5,8 +5,9 @@ Tolerances (written here, derived in the design notes):
   differ only in rounding order), and rho, u, B to relative L2 <= 1e-12 after the full
   2000-step Kelvin-Helmholtz run of the 64x64 configuration, whose oracle-vs-oracle floor for a
   1-ulp change of the initial state stays below 1e-13.
-* FP32 (f - w and g stored in binary32, binary32 collision): relative L2 against the FP64
-  oracle at fixed step counts before the jet saturates, bounds stated per case below.
+* FP32 and FP16 (f - w and g stored in binary32 / binary16, binary32 collision): relative L2
+  against the FP64 oracle at fixed step counts before the jet saturates, bounds stated per
+  case below.
 """
 import os
 
@@ -131,6 +132,31 @@ def test_fp32_kh_jet_64_against_fp64_oracle(steps, tol_u, tol_b):
     assert rl2(np.stack(mom[3:5]), np.stack(omom[3:5])) < tol_b
 
 
+@pytest.mark.parametrize("steps,tol_u,tol_b", [(100, 2e-3, 2e-3), (500, 3e-3, 4e-3),
+                                               (1000, 4e-3, 6e-3)])
+def test_fp16_kh_jet_64_against_fp64_oracle(steps, tol_u, tol_b):
+    """FP16 storage of f - w and g (binary16: 11-bit significand) with binary32 collision,
+    against the FP64 oracle: relative L2 of rho and of the vector fields u and B.  Scale of the
+    bound: binary16 rounds the O(0.02) deviations to ~1e-5 absolute per store, ~2e-4 of |u| per
+    step (measured 8.3e-4 / 1.2e-3 / 1.9e-3 for u and 9.4e-4 / 1.8e-3 / 3.0e-3 for B)."""
+    n = 64
+    fields = kh_jet(n, seed=1)
+    s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
+    _, _, mom, omom = run_pair(fields, s, sm, 2.0, steps, precision=lbmhd.LBMHD_FP16)
+    assert rl2(mom[0], omom[0]) < 1.5e-4
+    assert rl2(np.stack(mom[1:3]), np.stack(omom[1:3])) < tol_u
+    assert rl2(np.stack(mom[3:5]), np.stack(omom[3:5])) < tol_b
+
+
+@pytest.mark.parametrize("nx,ny,stencil", [(300, 70, 0), (33, 17, 1), (3, 3, 0)])
+def test_fp16_short_runs_elementwise(nx, ny, stencil):
+    fields = smooth_random_fields(nx, ny, seed=3, amp_u=0.05, amp_b=0.04, amp_rho=0.02)
+    s, sm = mrt_rates(0.01), oracle.rate_from_diffusivity(0.015)
+    pops, ref, _, _ = run_pair(fields, s, sm, 2.0, 6, precision=lbmhd.LBMHD_FP16, stencil=stencil)
+    # binary16 deviations of O(0.02-0.1): half an ulp is 1e-5..5e-5 per store (measured 1.9e-5)
+    assert np.max(np.abs(pops - ref)) < 6e-5
+
+
 @pytest.mark.parametrize("nx,ny,stencil", [(300, 70, 0), (33, 17, 1), (3, 3, 0)])
 def test_fp32_short_runs_elementwise(nx, ny, stencil):
     fields = smooth_random_fields(nx, ny, seed=3, amp_u=0.05, amp_b=0.04, amp_rho=0.02)
@@ -174,6 +200,13 @@ def test_full_size_2048_fp32_dns_sampled():
 @pytest.mark.slow
 def test_full_size_2048_fp32_les_sampled():
     _sampled_full_size(2048, lbmhd.LBMHD_FP32, 2.0, 5e-4, 50, 1e-7)
+
+
+@pytest.mark.slow
+def test_full_size_2048_fp16_les_sampled():
+    # the GPU state is binary16; the oracle collides it in binary64: one binary16 rounding
+    # of each stored result (|value| < 0.1) is at most ~3e-5
+    _sampled_full_size(2048, lbmhd.LBMHD_FP16, 2.0, 5e-4, 50, 1e-4)
 
 
 @pytest.mark.slow
