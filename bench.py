@@ -38,14 +38,15 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS and % HBM roofline per LES-LB-MHD step vs plain FP64 step, at stated L2 err"
 BYTES_PER_CELL = {"fp16": 108, "fp32": 216, "fp64": 432}   # 27 populations read + 27 written
 FP64_ALU_TFLOPS = 1.25   # measured binary64 FMA throughput of this GB300 (independent chains)
+FP64_INSTR_PER_CELL = 216  # binary64 instructions per cell-update of the FP64 step (ncu)
 NU = ETA = 2e-3   # see the module docstring
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the fused FP32 kernel on the
 # 2048^2 workload, from an ncu capture; keyed by the SHA-256 of the kernel source it was taken
 # on, so a changed kernel reports null until it is measured again.
 MEASURED_TRAFFIC = {
-    # profiles/fused_step_fp32_2048.md: (470.48 + 408.27 + 470.53 + 408.81) MB / 2 launches
-    ("feb6a15ff93569bc", 2048, "fp32", 0.0): 879.05e6,
+    # profiles/fused_step_fp32_2048.md: (470.36 + 408.21 + 470.42 + 405.73) MB / 2 launches
+    ("36072e93d9cf29ee", 2048, "fp32", 0.0): 877.36e6,
 }
 
 
@@ -320,11 +321,15 @@ def side_measurements(n, a):
         return ms / k
 
     ms64 = rate(make_sim(n, "fp64", a.delta)[0], 400)
-    # ~270 binary64 operations per cell-update (ncu instruction counts), FMA counted once
+    # 216 binary64 instructions per cell-update (ncu: 121 DADD + 64 DFMA + 31 DMUL); the ALU
+    # peak is the measured DFMA issue rate, FP64_ALU_TFLOPS / 2 instructions per second
+    instr_rate = FP64_INSTR_PER_CELL * n * n / (ms64 * 1e-3)
     res["fp64_step"] = {"mlups": round(n * n / ms64 / 1e3, 2), "ms_per_step": round(ms64, 5),
                         "hbm_frac": round(BYTES_PER_CELL["fp64"] * n * n / (ms64 * 1e-3) / 1e9 /
                                           peaks()[0], 4),
-                        "bound": "alu (binary64)", "alu_peak_tflops": FP64_ALU_TFLOPS}
+                        "roofline": {"bound": "alu", "achieved": round(instr_rate / 1e9, 1),
+                                     "peak": FP64_ALU_TFLOPS / 2 * 1e3, "unit": "G binary64 instr/s",
+                                     "frac": round(instr_rate / (FP64_ALU_TFLOPS / 2 * 1e12), 4)}}
     ms16 = rate(make_sim(n, "fp16", a.delta)[0], 2000)
     res["fp16_step"] = {"mlups": round(n * n / ms16 / 1e3, 2), "ms_per_step": round(ms16, 5),
                         "hbm_frac": round(BYTES_PER_CELL["fp16"] * n * n / (ms16 * 1e-3) / 1e9 /
