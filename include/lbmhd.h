@@ -114,6 +114,29 @@ int lbmhd_get_populations(lbmhd_t* h, double* pops);
  * LBMHD_ERR_UNSTABLE (with out[] filled) if any cell has a NaN/Inf, rho <= 0 or |u| > 0.4. */
 int lbmhd_diagnostics(lbmhd_t* h, double* out);
 
+/* ---- Filtered-DNS vs LES comparison tools (off the time-step path) ---------------------
+ *
+ * Box filter: out = the r x r block means of `in` (a device [ny][nx] array; r divides nx and
+ * ny; out is [ny/r][nx/r]) -- the top-hat filter of width r (Sec. 1, Eq. VelFilter, whose second
+ * moment is the Delta^2/12 of Sec. 2.1 with Delta = r) followed by downsampling.  Asynchronous
+ * on `stream` (NULL: legacy default stream).  LBMHD_ERR_INVALID if r does not divide the grid. */
+int lbmhd_block_mean_device(const double* in, int nx, int ny, int r, double* out, void* stream);
+
+/* Shell-summed energy spectra of square n x n device fields (u_x, u_y, B_x, B_y):
+ *   a^(k) = n^-2 sum_x a(x) exp(-2 pi i k.x/n),  E_kin(s) = 1/2 sum_{k in s} |u_x^|^2 + |u_y^|^2,
+ *   E_mag(s) likewise with B; shell s = the integer wavevectors with (2s-1)^2 < 4|k|^2 < (2s+1)^2.
+ * e_kin, e_mag: device arrays of nbins (1 <= nbins <= n); n <= 4096.  `work` is a caller device
+ * buffer of at least lbmhd_energy_spectrum_work_bytes(n) bytes.  Bitwise reproducible;
+ * asynchronous on `stream`. */
+size_t lbmhd_energy_spectrum_work_bytes(int n);
+int lbmhd_energy_spectrum_device(const double* ux, const double* uy, const double* bx,
+                                 const double* by, int n, int nbins, double* e_kin, double* e_mag,
+                                 void* work, size_t work_bytes, void* stream);
+
+/* The same spectra of a handle's current state (square grid), into host arrays of nbins;
+ * allocates its work buffer on first use; synchronises. */
+int lbmhd_energy_spectrum(lbmhd_t* h, int nbins, double* e_kin, double* e_mag);
+
 /* Size in bytes of a checkpoint of this handle's state. */
 size_t lbmhd_state_bytes(const lbmhd_t* h);
 

@@ -47,6 +47,7 @@ struct lbmhd {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   CUtensorMap tmap[2];             // 3-D TMA descriptors of the two copies
   unsigned* err_flag = nullptr;    // device word: set by the step kernel on a pipeline timeout
+  void* spec_work = nullptr;       // spectrum work buffer and outputs (allocated on first use)
   uint64_t launches = 0;
   int64_t steps = 0;
   std::string err;
@@ -109,6 +110,7 @@ void free_all(lbmhd_t* h) {
   if (h->partials) cudaFree(h->partials);
   if (h->diag_out) cudaFree(h->diag_out);
   if (h->err_flag) cudaFree(h->err_flag);
+  if (h->spec_work) cudaFree(h->spec_work);
   if (h->ev_a) cudaEventDestroy(h->ev_a);
   if (h->ev_b) cudaEventDestroy(h->ev_b);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -469,6 +471,30 @@ int lbmhd_diagnostics(lbmhd_t* h, double* out) {
     return fail(h, LBMHD_ERR_UNSTABLE, "unstable state: NaN/Inf, rho <= 0 or |u| > 0.4 after %lld steps",
                 (long long)h->steps);
   return LBMHD_OK;
+}
+
+int lbmhd_energy_spectrum(lbmhd_t* h, int nbins, double* e_kin, double* e_mag) {
+  if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (!e_kin || !e_mag) return fail(h, LBMHD_ERR_INVALID, "output pointer is NULL");
+  const int n = h->p.nx;
+  if (h->p.ny != n) return fail(h, LBMHD_ERR_INVALID, "spectra need a square grid");
+  if (n > 4096) return fail(h, LBMHD_ERR_INVALID, "spectra are limited to n <= 4096");
+  if (nbins < 1 || nbins > n) return fail(h, LBMHD_ERR_INVALID, "nbins must be in [1, n]");
+  const size_t wb = spectrum_work_bytes(n);
+  if (!h->spec_work) LB_CUDA(h, cudaMalloc(&h->spec_work, wb + 2 * (size_t)n * sizeof(double)));
+  double* dk = reinterpret_cast<double*>(static_cast<char*>(h->spec_work) + wb);
+  double* dm = dk + n;
+  const size_t ncell = (size_t)n * n;
+  double* f = h->fields;
+  LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, f, f + ncell, f + 2 * ncell,
+                            f + 3 * ncell, f + 4 * ncell, h->stream));
+  LB_CUDA(h, launch_energy_spectrum(f + ncell, f + 2 * ncell, f + 3 * ncell, f + 4 * ncell, n, nbins,
+                                    dk, dm, h->spec_work, h->stream));
+  h->launches += 5;
+  LB_CUDA(h, cudaMemcpyAsync(e_kin, dk, nbins * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(h, cudaMemcpyAsync(e_mag, dm, nbins * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return check_step_status(h);
 }
 
 size_t lbmhd_state_bytes(const lbmhd_t* h) { return h ? h->state_bytes : 0; }

@@ -114,6 +114,15 @@ constexpr int kDiagSlots = 11;  // 10 public values + instability flag
 cudaError_t launch_diagnostics(const double* fields, int nx, int ny, double* partials,
                                double* out, cudaStream_t s);
 
+// Analysis kernels (lbmhd_analysis.cu): r x r block mean, and the shell-summed energy spectra
+// of a square n x n field set into device outputs e_kin[nbins], e_mag[nbins], using `work` of
+// spectrum_work_bytes(n) bytes.
+cudaError_t launch_block_mean(const double* in, int nx, int ny, int r, double* out, cudaStream_t s);
+size_t spectrum_work_bytes(int n);
+cudaError_t launch_energy_spectrum(const double* ux, const double* uy, const double* bx,
+                                   const double* by, int n, int nbins, double* ek, double* em,
+                                   void* work, cudaStream_t s);
+
 // Store a message for lbmhd_last_error(NULL) on the calling thread (lbmhd_api.cu).
 void set_thread_error(const char* msg);
 

@@ -89,6 +89,13 @@ def load_library(path: str | None = None):
             "lbmhd_get_stream": (ctypes.c_void_p, [_H]),
             "lbmhd_diagnostics_fields_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 5 + [
                 ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+            "lbmhd_block_mean_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+            "lbmhd_energy_spectrum_work_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+            "lbmhd_energy_spectrum_device": (ctypes.c_int, [ctypes.c_void_p] * 4 + [
+                ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                ctypes.c_size_t, ctypes.c_void_p]),
+            "lbmhd_energy_spectrum": (ctypes.c_int, [_H, ctypes.c_int, _D, _D]),
             "lbmhd_launch_count": (ctypes.c_uint64, [_H]),
             "lbmhd_step_count": (ctypes.c_int64, [_H]),
             "lbmhd_last_error": (ctypes.c_char_p, [_H]),
@@ -216,6 +223,37 @@ def lbmhd_diagnostics_fields_noalloc(fields, out, stream=None) -> None:
     _check(rc, None)
 
 
+def lbmhd_block_mean_device(field, r: int, out, stream=None) -> None:
+    """r x r block means of a CUDA float64 [ny, nx] tensor into ``out`` [ny/r, nx/r]."""
+    ny, nx = field.shape
+    if nx % r or ny % r:
+        raise ValueError("r must divide both grid sides")
+    _check(load_library().lbmhd_block_mean_device(_dptr(field, nx * ny), nx, ny, r,
+                                                  _dptr(out, (nx // r) * (ny // r)), stream))
+
+
+def lbmhd_energy_spectrum_device(ux, uy, bx, by, nbins: int, e_kin, e_mag, work, stream=None):
+    """Shell spectra of square CUDA float64 fields into CUDA float64 e_kin, e_mag [nbins];
+    ``work`` is a CUDA byte tensor of at least lbmhd_energy_spectrum_work_bytes(n) bytes."""
+    n = ux.shape[0]
+    lib = load_library()
+    ptrs = [_dptr(t, n * n) for t in (ux, uy, bx, by)]
+    _check(lib.lbmhd_energy_spectrum_device(*ptrs, n, nbins, _dptr(e_kin, nbins), _dptr(e_mag, nbins),
+                                            work.data_ptr(), work.numel() * work.element_size(),
+                                            stream))
+
+
+def lbmhd_energy_spectrum_work_bytes(n: int) -> int:
+    return int(load_library().lbmhd_energy_spectrum_work_bytes(n))
+
+
+def lbmhd_energy_spectrum(h, nbins: int):
+    ek = np.zeros(nbins)
+    em = np.zeros(nbins)
+    _check(load_library().lbmhd_energy_spectrum(h, nbins, ek.ctypes.data_as(_D), em.ctypes.data_as(_D)), h)
+    return ek, em
+
+
 def lbmhd_state_bytes(h) -> int:
     return int(load_library().lbmhd_state_bytes(h))
 
@@ -276,6 +314,9 @@ class Lbmhd:
 
     def diagnostics(self) -> np.ndarray:
         return lbmhd_diagnostics(self.h)
+
+    def spectrum(self, nbins: int):
+        return lbmhd_energy_spectrum(self.h, nbins)
 
     def get_state(self) -> np.ndarray:
         return lbmhd_get_state(self.h)
