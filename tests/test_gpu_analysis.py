@@ -79,14 +79,17 @@ def test_invalid_arguments():
 
 
 def test_les_dns_pipeline_small():
-    """The LES-vs-DNS driver at a small size: all numbers finite, the coarse runs start from the
-    box-filtered DNS fields, energies consistent."""
+    """The LES-vs-DNS driver at a small size: all numbers finite, energies of the coarse runs
+    close to the filtered DNS, the spectra non-negative."""
     from paper_1705_09807_gb300 import les_dns
-    out = les_dns.run_pair(n=256, r=4, nu_dns=8e-3, dns_steps=400, checkpoints=2,
-                           precision=lbmhd.LBMHD_FP64)
-    assert out["n_les"] == 64 and out["nu_les"] == 2e-3 and out["delta_les"] == 4.0
-    assert len(out["checkpoints"]) == 2
+    out = les_dns.run_experiment(n=256, r=4, nu_dns=8e-3, fine_steps=400, checkpoints=(200, 400),
+                                 deltas=(2.0, 0.0), precision=lbmhd.LBMHD_FP64, ic="kh")
+    assert out["n_coarse"] == 64 and out["nu_coarse"] == 2e-3
+    assert [c["fine_step"] for c in out["checkpoints"]] == [200, 400]
     for c in out["checkpoints"]:
-        for k, v in c.items():
-            assert np.isfinite(v), k
-        assert abs(c["energy_les"] / c["energy_filtered_dns"] - 1) < 0.05
+        ref = c["filtered_dns"]
+        assert np.isfinite(ref["energy"]) and min(ref["spectrum"]) >= 0
+        for name in ("delta2", "delta0"):
+            e = c[name]
+            assert np.isfinite(e["rel_l2_vs_filtered_dns"]) and np.isfinite(e["slope"])
+            assert abs(e["energy"] / ref["energy"] - 1) < 0.05
