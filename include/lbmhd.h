@@ -137,6 +137,42 @@ int lbmhd_energy_spectrum_device(const double* ux, const double* uy, const doubl
  * allocates its work buffer on first use; synchronises. */
 int lbmhd_energy_spectrum(lbmhd_t* h, int nbins, double* e_kin, double* e_mag);
 
+/* ---- Ensembles: many independent runs, one launch per time step -------------------------
+ *
+ * An ensemble owns n member runs (each its own grid size, rates and filter width; all with the
+ * same precision and gradient stencil) and advances all of them with ONE kernel launch per time
+ * step: the launch walks a work list of tiles (member, 128-column strip, band of rows), either
+ * one block per tile or persistent blocks taking tiles from an atomic counter.  With an
+ * ensemble-owned stream, whole groups of 32 steps are replayed from a captured CUDA graph.
+ * Members are ordinary handles for every read-out call (moments, populations, diagnostics,
+ * spectra, checkpoints); lbmhd_step on a member is refused and lbmhd_free on it is a no-op.
+ *
+ * fields: 5*n host pointers, rho, ux, uy, bx, by of member 0, then member 1, ... ([ny][nx] each,
+ * copied).  cuda_stream: NULL = the ensemble creates its own stream (and uses graphs). */
+typedef struct lbmhd_ensemble lbmhd_ensemble_t;
+int lbmhd_ensemble_create(lbmhd_ensemble_t** out, int n, const lbmhd_params* params,
+                          const double* const* fields, void* cuda_stream);
+/* Advance every member by nsteps (asynchronous on the ensemble's stream). */
+int lbmhd_ensemble_step(lbmhd_ensemble_t* e, int nsteps);
+/* Tile schedule: rows_per_tile = 0 gives each member its one-wave band height; persistent = 1
+ * launches one resident wave of blocks that take tiles from an atomic counter. */
+int lbmhd_ensemble_set_schedule(lbmhd_ensemble_t* e, int rows_per_tile, int persistent);
+int lbmhd_ensemble_get_schedule(const lbmhd_ensemble_t* e, int* rows_per_tile, int* persistent,
+                                int* nwork, int* grid);
+/* Autotuner: times trial_steps steps of each candidate schedule (rows per tile in {one-wave,
+ * 8, 16, 32, 64, 128, 256} x {one block per tile, persistent}), keeps the fastest, and restores
+ * every member's state and step count.  *best_ms (may be NULL) receives its time per step. */
+int lbmhd_ensemble_autotune(lbmhd_ensemble_t* e, int trial_steps, double* best_ms);
+/* Wait for the ensemble's stream; LBMHD_ERR_TIMEOUT if a pipeline wait ran out. */
+int lbmhd_ensemble_sync(lbmhd_ensemble_t* e);
+/* Member i as a handle for read-out calls (borrowed; valid until lbmhd_ensemble_free). */
+lbmhd_t* lbmhd_ensemble_member(lbmhd_ensemble_t* e, int i);
+int lbmhd_ensemble_size(const lbmhd_ensemble_t* e);
+void* lbmhd_ensemble_get_stream(const lbmhd_ensemble_t* e);
+uint64_t lbmhd_ensemble_launch_count(const lbmhd_ensemble_t* e);
+const char* lbmhd_ensemble_last_error(const lbmhd_ensemble_t* e);
+void lbmhd_ensemble_free(lbmhd_ensemble_t* e);
+
 /* Size in bytes of a checkpoint of this handle's state. */
 size_t lbmhd_state_bytes(const lbmhd_t* h);
 

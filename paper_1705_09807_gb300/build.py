@@ -19,7 +19,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbmhd.so")
-SOURCES = ["lbmhd_step.cu", "lbmhd_aux.cu", "lbmhd_api.cu", "lbmhd_noalloc.cu", "lbmhd_analysis.cu"]
+SOURCES = ["lbmhd_step.cu", "lbmhd_aux.cu", "lbmhd_api.cu", "lbmhd_noalloc.cu", "lbmhd_analysis.cu",
+           "lbmhd_ensemble.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

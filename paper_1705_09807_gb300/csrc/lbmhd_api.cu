@@ -14,6 +14,7 @@
 #include <string>
 
 #include "lbmhd.h"
+#include "lbmhd_handle.h"
 #include "lbmhd_internal.cuh"
 
 using namespace lbmhd_gpu;
@@ -28,30 +29,6 @@ thread_local std::string g_tls_error;
 
 void lbmhd_gpu::set_thread_error(const char* msg) { g_tls_error = msg ? msg : ""; }
 
-struct lbmhd {
-  lbmhd_params p{};
-  int precision = 0;
-  int device = 0;
-  StepGeom geom{};
-  StepCoef coef{};
-  size_t elem = 8;         // bytes per stored population value
-  size_t state_bytes = 0;  // one population copy
-  void* pops[2] = {nullptr, nullptr};
-  int cur = 0;             // copy holding the current state
-  double* fields = nullptr;    // 5 x nx*ny moment fields (moments / diagnostics)
-  double* partials = nullptr;  // diagnostics block partials
-  double* diag_out = nullptr;  // kDiagSlots results
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  cudaEvent_t ev_a = nullptr, ev_b = nullptr;  // ordering with the legacy default stream
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  CUtensorMap tmap[2];             // 3-D TMA descriptors of the two copies
-  unsigned* err_flag = nullptr;    // device word: set by the step kernel on a pipeline timeout
-  void* spec_work = nullptr;       // spectrum work buffer and outputs (allocated on first use)
-  uint64_t launches = 0;
-  int64_t steps = 0;
-  std::string err;
-};
 
 namespace {
 
@@ -305,6 +282,17 @@ int check_fields(const double* a, const double* b, const double* c, const double
 
 }  // namespace
 
+int lbmhd_gpu::create_handle(lbmhd_t** out, const lbmhd_params* p) { return create(out, p); }
+void lbmhd_gpu::destroy_handle(lbmhd_t* h) { free_all(h); }
+int lbmhd_gpu::handle_fail(lbmhd_t* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  return fail(h, code, "%s", buf);
+}
+
 extern "C" {
 
 int lbmhd_params_srt(lbmhd_params* p, int nx, int ny, double nu, double eta, double delta,
@@ -385,6 +373,8 @@ int lbmhd_init_device(lbmhd_t** out, const lbmhd_params* p, const double* rho,
 
 int lbmhd_step(lbmhd_t* h, int nsteps) {
   if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (h->in_ensemble)
+    return fail(h, LBMHD_ERR_INVALID, "this handle is an ensemble member: step the ensemble");
   if (nsteps < 0) return fail(h, LBMHD_ERR_INVALID, "nsteps = %d < 0", nsteps);
   int n = nsteps;
   // whole graphs of kGraphSteps launches when the handle owns its stream
@@ -529,6 +519,9 @@ const char* lbmhd_last_error(const lbmhd_t* h) {
   return g_tls_error.c_str();
 }
 
-void lbmhd_free(lbmhd_t* h) { free_all(h); }
+void lbmhd_free(lbmhd_t* h) {
+  if (h && h->in_ensemble) return;  // owned by its ensemble
+  free_all(h);
+}
 
 }  // extern "C"

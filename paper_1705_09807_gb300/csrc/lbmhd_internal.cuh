@@ -98,6 +98,18 @@ int step_band_rows(int nx, int ny, int precision, int num_sms);
 // Opt the step kernels in to their dynamic shared memory (once per process and device).
 cudaError_t prepare_step_kernels();
 
+// Ensemble step (lbmhd_step.cu): the member table is packed on the host into
+// ensemble_member_bytes(precision) * n bytes and copied to the device; work[i] = {member,
+// strip x0, band start y0, band index}; queue == nullptr takes tiles by a static stride,
+// otherwise from the zeroed atomic counter *queue.
+size_t ensemble_member_bytes(int precision);
+void pack_ensemble_members(int precision, int n, const CUtensorMap* maps, void* const* pops,
+                           const StepGeom* geoms, const StepCoef* coefs, void* host_out);
+cudaError_t launch_ensemble_step(int precision, int stencil, const void* members, const int4* work,
+                                 int nwork, int parity, unsigned long long* queue, int grid,
+                                 unsigned* err, cudaStream_t s);
+int resident_step_blocks(int precision, int num_sms);
+
 // Auxiliary kernels (lbmhd_aux.cu).  `precision` selects double / float / half storage.
 cudaError_t launch_init_eq(int precision, void* pops, const StepGeom& g, const double* rho,
                            const double* ux, const double* uy, const double* bx, const double* by,

@@ -178,29 +178,45 @@ __device__ __forceinline__ void moments_from(const S* st, int ge, int col, C& rh
   by = ((v(18) + v(19)) + (v(20) + v(21))) + ((v(22) + v(23)) + (v(24) + v(25))) + v(26);
 }
 
-template <typename S, int ISO, int NST, int MINB>
-__global__ void __launch_bounds__(kStepThreads, MINB)
-    fused_step_kernel(const __grid_constant__ CUtensorMap src, S* __restrict__ dst, StepGeom g,
-                      KCoef<typename ArithOf<S>::type> c, unsigned* __restrict__ err) {
+// Dynamic shared memory of a step block, rounded up to the 128-byte alignment TMA needs.
+template <typename S, int NST>
+__device__ __forceinline__ StepSmem<S, NST>& step_smem() {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  return *reinterpret_cast<StepSmem<S, NST>*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+}
+
+template <typename S, int NST>
+__device__ __forceinline__ void init_stage_barriers(StepSmem<S, NST>& S_, const CUtensorMap* prefetch) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) mbar_init(&S_.full[s], 1);
+    fence_barrier_init();
+    if (prefetch) prefetch_tmap(prefetch);
+  }
+}
+
+// One tile: the strip of kStepThreads columns starting at x0 and the band of rows [y0, y0 + band)
+// of one grid, marched in direction +1 (band_parity even) or -1 (odd).  `kbase` counts the rows
+// this block has staged before this tile, so stage slots and mbarrier phases continue across
+// tiles.  Returns false if a wait timed out (the block must stop; *err is set).
+template <typename S, int ISO, int NST>
+__device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict__ dst, const StepGeom& g,
+                                         const KCoef<typename ArithOf<S>::type>& c, int x0, int y0,
+                                         int band_parity, uint32_t& kbase, unsigned* __restrict__ err) {
   using SM = StepSmem<S, NST>;
   using T = typename SM::C;
   constexpr int GE = SM::kGroupElems;
   constexpr int LEAD = SM::kLead;
   constexpr int BW = SM::kBoxW;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  // TMA destinations need 128-byte alignment: round the dynamic base up (slack reserved)
-  SM& S_ = *reinterpret_cast<SM*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+  SM& S_ = step_smem<S, NST>();
 
   const int t = threadIdx.x;
   const int nx = g.nx, ny = g.ny;
-  const int x0 = blockIdx.x * kStepThreads;
   const int ncol = min(kStepThreads, nx - x0);
   const bool active = t < ncol;
-  const int y0 = blockIdx.y * g.band;
-  if (y0 >= ny) return;  // uniform per block
   const int y1 = min(y0 + g.band, ny);
   const int L = (y1 - y0) + 2;  // rows staged: the band and one on each side
-  const int dir = (blockIdx.y & 1) ? -1 : 1;
+  const int dir = (band_parity & 1) ? -1 : 1;
+  const uint32_t kb = kbase;
   // k-th row in march order (k = 0 and L-1 are the neighbours' rows)
   auto row_of = [&](int k) -> int {
     int r = dir > 0 ? y0 - 1 + k : y1 - k;
@@ -209,23 +225,26 @@ __global__ void __launch_bounds__(kStepThreads, MINB)
     return r;
   };
   auto issue = [&](int k) {
-    const int s = k % NST;
+    const uint32_t K = kb + (uint32_t)k;
+    const int s = (int)(K % NST);
     const int r = row_of(k);
     const int ra = r == 0 ? ny - 1 : r - 1;  // c_y = +1 group is pulled from row r - 1
     const int rc = r == ny - 1 ? 0 : r + 1;  // c_y = -1 group from row r + 1
     const int cx = x0 + kXOff - LEAD;        // box covers logical columns x0-LEAD .. x0+BW-LEAD-1
     mbar_arrive_expect_tx(&S_.full[s], SM::kTxBytes);
-    tma_load_3d(&S_.stage[s][0], &src, cx, ra, 0, &S_.full[s]);
-    tma_load_3d(&S_.stage[s][GE], &src, cx, r, 9, &S_.full[s]);
-    tma_load_3d(&S_.stage[s][2 * GE], &src, cx, rc, 18, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][0], srcp, cx, ra, 0, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][GE], srcp, cx, r, 9, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][2 * GE], srcp, cx, rc, 18, &S_.full[s]);
   };
+  auto slot = [&](int k) -> int { return (int)((kb + (uint32_t)k) % NST); };
   auto wait_row = [&](int k) -> bool {
-    return mbar_wait_bounded(&S_.full[k % NST], (uint32_t)((k / NST) & 1), kWaitLimitNs);
+    const uint32_t K = kb + (uint32_t)k;
+    return mbar_wait_bounded(&S_.full[K % NST], (K / NST) & 1u, kWaitLimitNs);
   };
   // moments of staged row k into ring slot k & 3 (own column and the strip's halo columns)
   T rho_next = T(0);
   auto ring_moments = [&](int k) {
-    const S* st = S_.stage[k % NST];
+    const S* st = S_.stage[slot(k)];
     T* rg = &S_.ring[k & (kRing - 1)][0][0];
     constexpr int RS = kStepThreads + 2;
     T r1, jx, jy, bx, by;
@@ -254,16 +273,15 @@ __global__ void __launch_bounds__(kStepThreads, MINB)
   };
 
   if (t == 0) {
-    for (int s = 0; s < NST; ++s) mbar_init(&S_.full[s], 1);
     S_.abort_flag[0] = 0;
     S_.abort_flag[1] = 0;
-    fence_barrier_init();
-    prefetch_tmap(&src);
   }
-  __syncthreads();
+  __syncthreads();  // barriers initialised / the previous tile's shared memory released
   const int first = NST < L ? NST : L;
-  if (t == 0)
+  if (t == 0) {
+    fence_proxy_async_smem();
     for (int k = 0; k < first; ++k) issue(k);
+  }
   int issued = first;  // meaningful in thread 0 only
 
   // prologue: rows k = 0 and k = 1
@@ -282,7 +300,7 @@ __global__ void __launch_bounds__(kStepThreads, MINB)
         atomicOr(err, 1u);
         for (int k = m + 1; k < issued; ++k) wait_row(k);  // drain copies still in flight
       }
-      return;
+      return false;
     }
     if (t == 0 && m - 1 + NST < L) {
       fence_proxy_async_smem();
@@ -322,7 +340,7 @@ __global__ void __launch_bounds__(kStepThreads, MINB)
         }
       }
       const T jx = rc[0 * RS + si], jy = rc[1 * RS + si], bx = rc[2 * RS + si], by = rc[3 * RS + si];
-      const S* st = S_.stage[m % NST];
+      const S* st = S_.stage[slot(m)];
       T p[kQ];
 #pragma unroll
       for (int q = 0; q < kQ; ++q) p[q] = staged<T, S, BW>(st, GE, q, t + LEAD);
@@ -342,6 +360,61 @@ __global__ void __launch_bounds__(kStepThreads, MINB)
       }
     }
     rho_cur = rho_next;
+  }
+  kbase = kb + (uint32_t)L;
+  return true;
+}
+
+// One grid: block (strip, band) = one tile.
+template <typename S, int ISO, int NST, int MINB>
+__global__ void __launch_bounds__(kStepThreads, MINB)
+    fused_step_kernel(const __grid_constant__ CUtensorMap src, S* __restrict__ dst, StepGeom g,
+                      KCoef<typename ArithOf<S>::type> c, unsigned* __restrict__ err) {
+  if ((int)blockIdx.y * g.band >= g.ny) return;  // uniform per block
+  init_stage_barriers(step_smem<S, NST>(), &src);
+  uint32_t kbase = 0;
+  run_tile<S, ISO, NST>(&src, dst, g, c, blockIdx.x * kStepThreads, blockIdx.y * g.band, blockIdx.y,
+                        kbase, err);
+}
+
+// Ensemble: every member grid advances one step in this launch.  work[i] = {member, x0, y0,
+// band index}; blocks take tiles either by a static stride over the list (queue == nullptr) or
+// from an atomic counter (persistent blocks; the counter is zeroed before each launch).
+template <typename S>
+struct EnsembleMember {
+  CUtensorMap map[2];  // tensor maps of the member's two population copies (64-byte aligned)
+  S* pops[2];
+  StepGeom g;
+  KCoef<typename ArithOf<S>::type> c;
+};
+
+template <typename S, int ISO, int NST, int MINB>
+__global__ void __launch_bounds__(kStepThreads, MINB)
+    ensemble_step_kernel(const EnsembleMember<S>* __restrict__ members, const int4* __restrict__ work,
+                         int nwork, int parity, unsigned long long* queue, unsigned* __restrict__ err) {
+  __shared__ int next_item;
+  init_stage_barriers(step_smem<S, NST>(), nullptr);
+  uint32_t kbase = 0;
+  int w = blockIdx.x;
+  if (queue) {
+    if (threadIdx.x == 0) next_item = (int)atomicAdd(queue, 1ull);
+    __syncthreads();
+    w = next_item;
+  }
+  while (w < nwork) {
+    const int4 it = work[w];
+    const EnsembleMember<S>& mb = members[it.x];
+    if (!run_tile<S, ISO, NST>(&mb.map[parity], mb.pops[parity ^ 1], mb.g, mb.c, it.y, it.z, it.w,
+                               kbase, err))
+      return;
+    if (queue) {
+      __syncthreads();  // everyone has read next_item before it is overwritten
+      if (threadIdx.x == 0) next_item = (int)atomicAdd(queue, 1ull);
+      __syncthreads();
+      w = next_item;
+    } else {
+      w += gridDim.x;
+    }
   }
 }
 
@@ -420,13 +493,47 @@ cudaError_t launch_step(const CUtensorMap& src, S* dst, const StepGeom& g, const
   return cudaGetLastError();
 }
 
+template <typename S, int ISO>
+constexpr auto ensemble_kernel_ptr() {
+  return &ensemble_step_kernel<S, ISO, StepConfig<S>::kStages, StepConfig<S>::kMinBlocks>;
+}
+
 template <typename S>
 cudaError_t set_smem_attr() {
-  cudaError_t e = cudaFuncSetAttribute(kernel_ptr<S, 0>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes<S>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kernel_ptr<S, 1>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_bytes<S>());
+  const int b = (int)smem_bytes<S>();
+  cudaError_t e = cudaFuncSetAttribute(kernel_ptr<S, 0>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel_ptr<S, 1>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ensemble_kernel_ptr<S, 0>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ensemble_kernel_ptr<S, 1>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  return e;
+}
+
+template <typename S>
+void pack_members(int n, const CUtensorMap* maps, void* const* pops, const StepGeom* geoms,
+                  const StepCoef* coefs, void* out) {
+  EnsembleMember<S>* m = static_cast<EnsembleMember<S>*>(out);
+  for (int i = 0; i < n; ++i) {
+    m[i].map[0] = maps[2 * i];
+    m[i].map[1] = maps[2 * i + 1];
+    m[i].pops[0] = static_cast<S*>(pops[2 * i]);
+    m[i].pops[1] = static_cast<S*>(pops[2 * i + 1]);
+    m[i].g = geoms[i];
+    m[i].c = cast_coef<typename ArithOf<S>::type>(coefs[i]);
+  }
+}
+
+template <typename S>
+cudaError_t launch_ens(int stencil, const void* members, const int4* work, int nwork, int parity,
+                       unsigned long long* queue, int grid, unsigned* err, cudaStream_t s) {
+  const EnsembleMember<S>* mb = static_cast<const EnsembleMember<S>*>(members);
+  if (stencil == 1)
+    ensemble_kernel_ptr<S, 1>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(mb, work, nwork, parity, queue, err);
+  else
+    ensemble_kernel_ptr<S, 0>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(mb, work, nwork, parity, queue, err);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -451,6 +558,33 @@ cudaError_t launch_step_f32(const CUtensorMap& src, float* dst, const StepGeom& 
 cudaError_t launch_step_f16(const CUtensorMap& src, __half* dst, const StepGeom& g,
                             const StepCoef& c, int stencil, unsigned* err, cudaStream_t s) {
   return launch_step<__half>(src, dst, g, c, stencil, err, s);
+}
+
+size_t ensemble_member_bytes(int precision) {
+  return precision == 0 ? sizeof(EnsembleMember<double>)
+                        : (precision == 1 ? sizeof(EnsembleMember<float>) : sizeof(EnsembleMember<__half>));
+}
+
+void pack_ensemble_members(int precision, int n, const CUtensorMap* maps, void* const* pops,
+                           const StepGeom* geoms, const StepCoef* coefs, void* host_out) {
+  if (precision == 0) pack_members<double>(n, maps, pops, geoms, coefs, host_out);
+  else if (precision == 1) pack_members<float>(n, maps, pops, geoms, coefs, host_out);
+  else pack_members<__half>(n, maps, pops, geoms, coefs, host_out);
+}
+
+cudaError_t launch_ensemble_step(int precision, int stencil, const void* members, const int4* work,
+                                 int nwork, int parity, unsigned long long* queue, int grid,
+                                 unsigned* err, cudaStream_t s) {
+  if (precision == 0) return launch_ens<double>(stencil, members, work, nwork, parity, queue, grid, err, s);
+  if (precision == 1) return launch_ens<float>(stencil, members, work, nwork, parity, queue, grid, err, s);
+  return launch_ens<__half>(stencil, members, work, nwork, parity, queue, grid, err, s);
+}
+
+int resident_step_blocks(int precision, int num_sms) {
+  const int per_sm = precision == 0   ? StepConfig<double>::kMinBlocks
+                     : precision == 1 ? StepConfig<float>::kMinBlocks
+                                      : StepConfig<__half>::kMinBlocks;
+  return num_sms * per_sm;
 }
 
 // Rows per block: with the blocks that fit on the GPU at once (`resident`), give every strip

@@ -97,6 +97,19 @@ def load_library(path: str | None = None):
                 ctypes.c_size_t, ctypes.c_void_p]),
             "lbmhd_energy_spectrum": (ctypes.c_int, [_H, ctypes.c_int, _D, _D]),
             "lbmhd_launch_count": (ctypes.c_uint64, [_H]),
+            "lbmhd_ensemble_create": (ctypes.c_int, [ctypes.POINTER(_H), ctypes.c_int, P,
+                                                     ctypes.POINTER(_D), ctypes.c_void_p]),
+            "lbmhd_ensemble_step": (ctypes.c_int, [_H, ctypes.c_int]),
+            "lbmhd_ensemble_set_schedule": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int]),
+            "lbmhd_ensemble_get_schedule": (ctypes.c_int, [_H] + [ctypes.POINTER(ctypes.c_int)] * 4),
+            "lbmhd_ensemble_autotune": (ctypes.c_int, [_H, ctypes.c_int, _D]),
+            "lbmhd_ensemble_sync": (ctypes.c_int, [_H]),
+            "lbmhd_ensemble_member": (ctypes.c_void_p, [_H, ctypes.c_int]),
+            "lbmhd_ensemble_size": (ctypes.c_int, [_H]),
+            "lbmhd_ensemble_get_stream": (ctypes.c_void_p, [_H]),
+            "lbmhd_ensemble_launch_count": (ctypes.c_uint64, [_H]),
+            "lbmhd_ensemble_last_error": (ctypes.c_char_p, [_H]),
+            "lbmhd_ensemble_free": (None, [_H]),
             "lbmhd_step_count": (ctypes.c_int64, [_H]),
             "lbmhd_last_error": (ctypes.c_char_p, [_H]),
             "lbmhd_free": (None, [_H]),
@@ -340,6 +353,92 @@ class Lbmhd:
         if self.h is not None:
             lbmhd_free(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- ensembles
+class Ensemble:
+    """Many independent runs advanced by one launch per step (lbmhd_ensemble_* in the C ABI).
+    ``members`` is a list of (params, (rho, ux, uy, bx, by)) with host numpy fields."""
+
+    def __init__(self, members, cuda_stream=None):
+        lib = load_library()
+        n = len(members)
+        self._params = (LbmhdParams * n)(*[p for p, _ in members])
+        self._fields = []
+        ptrs = (_D * (5 * n))()
+        for i, (p, f) in enumerate(members):
+            for k, a in enumerate(f):
+                a = _host(a, (p.ny, p.nx))
+                self._fields.append(a)
+                ptrs[5 * i + k] = a.ctypes.data_as(_D)
+        self.h = _H()
+        rc = lib.lbmhd_ensemble_create(ctypes.byref(self.h), n, self._params, ptrs, cuda_stream)
+        if rc != LBMHD_OK:
+            raise LbmhdError(rc, (lib.lbmhd_ensemble_last_error(None) or b"").decode())
+        self._fields = None
+        self.n = n
+        self.shapes = [(p.ny, p.nx) for p, _ in members]
+
+    def _check(self, rc):
+        if rc != LBMHD_OK:
+            raise LbmhdError(rc, (load_library().lbmhd_ensemble_last_error(self.h) or b"").decode())
+
+    def step(self, nsteps: int):
+        self._check(load_library().lbmhd_ensemble_step(self.h, int(nsteps)))
+        return self
+
+    def set_schedule(self, rows_per_tile: int, persistent: bool):
+        self._check(load_library().lbmhd_ensemble_set_schedule(self.h, rows_per_tile, int(persistent)))
+
+    def schedule(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        self._check(load_library().lbmhd_ensemble_get_schedule(self.h, *(ctypes.byref(x) for x in v)))
+        return {"rows_per_tile": v[0].value, "persistent": bool(v[1].value), "tiles": v[2].value,
+                "blocks": v[3].value}
+
+    def autotune(self, trial_steps: int = 20) -> float:
+        best = ctypes.c_double()
+        self._check(load_library().lbmhd_ensemble_autotune(self.h, trial_steps, ctypes.byref(best)))
+        return best.value
+
+    def sync(self):
+        self._check(load_library().lbmhd_ensemble_sync(self.h))
+
+    def member(self, i: int):
+        return _H(load_library().lbmhd_ensemble_member(self.h, i))
+
+    def moments(self, i: int):
+        ny, nx = self.shapes[i]
+        return lbmhd_moments(self.member(i), ny, nx)
+
+    def populations(self, i: int):
+        ny, nx = self.shapes[i]
+        return lbmhd_get_populations(self.member(i), ny, nx)
+
+    @property
+    def stream(self) -> int:
+        return int(load_library().lbmhd_ensemble_get_stream(self.h) or 0)
+
+    @property
+    def launches(self) -> int:
+        return int(load_library().lbmhd_ensemble_launch_count(self.h))
+
+    def free(self):
+        if self.h is not None and self.h.value:
+            load_library().lbmhd_ensemble_free(self.h)
+        self.h = None
 
     def __enter__(self):
         return self
