@@ -173,6 +173,58 @@ uint64_t lbmhd_ensemble_launch_count(const lbmhd_ensemble_t* e);
 const char* lbmhd_ensemble_last_error(const lbmhd_ensemble_t* e);
 void lbmhd_ensemble_free(lbmhd_ensemble_t* e);
 
+/* ---- Subgrid correction and the learned closure ------------------------------------------
+ *
+ * The collision's filtered equilibria carry four subgrid terms (Sec. 2.1 / Sec. 3): the xy
+ * stress in M_3 (c0), the normal-stress difference in M_4 (c1), the trace in M_7 and M_8 (c2,
+ * entering as -3 c2) and the electric field E of N^eq (c3).  The analytic closure gives each as
+ * Delta^2/12 times gradient products; a correction adds c0..c3 per cell on top of it.
+ *
+ * lbmhd_set_correction_device: a static correction, binary32 device planes corr[4][ny][nx]
+ * (caller-owned, read at every step; NULL detaches).  Binary64 / binary32 storage only. */
+int lbmhd_set_correction_device(lbmhd_t* h, const float* corr);
+
+/* The learned closure: a periodic 3x3 convolutional network 12 -> 32 -> 32 -> 4 channels (tanh
+ * after the first two layers; 13,892 binary32 parameters: per layer W[co][ci][dy+1][dx+1] then
+ * b[co]) mapping 12 features of the state -- u_x, u_y, B_x, B_y and their central differences
+ * d_x, d_y, each divided by in_scale[k] -- to the residual of the four subgrid terms with
+ * respect to the analytic closure, divided by out_scale[k].  Trained on box-filtered fine runs
+ * by the library's own binary32 forward / back-propagation / Adam kernels; applied with bf16
+ * operands on the tensor cores (binary32 accumulation). */
+typedef struct lbmhd_closure lbmhd_closure_t;
+int lbmhd_closure_num_params(void);
+int lbmhd_closure_create(lbmhd_closure_t** out, const float* params, const float* in_scale,
+                         const float* out_scale);
+int lbmhd_closure_get_params(lbmhd_closure_t* c, float* params);
+int lbmhd_closure_set_params(lbmhd_closure_t* c, const float* params);
+/* Training pair from a fine state: fine = device binary64 planes rho, ux, uy, bx, by [n][n];
+ * box filter r (r | n); x = features [12][n/r][n/r], t = targets [4][n/r][n/r] (device
+ * binary32): t = (exact filtered subgrid term - analytic closure with filter width delta, in
+ * coarse lattice units) / out_scale.  work: device buffer of 9 (n/r)^2 doubles. Synchronises. */
+int lbmhd_closure_training_pair(lbmhd_closure_t* c, const double* fine, int n, int r, double delta,
+                                float* x, float* t, double* work);
+/* Features (and optionally the analytic closure, 4 planes, physical units) of a coarse state
+ * given as device binary64 planes rho, ux, uy, bx, by [m][m].  Synchronises. */
+int lbmhd_closure_features(lbmhd_closure_t* c, const double* state, int m, double delta, float* x,
+                           float* analytic);
+/* x: device [batch][12][h][w]; t: [batch][4][h][w]; mean-squared-error loss / 2.
+ * gradient: loss and the flat parameter gradient (host, may be NULL); train_step: one Adam step
+ * (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr.  Both synchronise. */
+int lbmhd_closure_gradient(lbmhd_closure_t* c, const float* x, const float* t, int batch, int h,
+                           int w, float* grad, double* loss);
+int lbmhd_closure_train_step(lbmhd_closure_t* c, const float* x, const float* t, int batch, int h,
+                             int w, float lr, double* loss);
+/* Network output (scaled units) for device features x into out [batch][4][h][w]:
+ * tensor_cores = 1 uses the bf16 mma path, 0 the binary32 path.  Synchronises. */
+int lbmhd_closure_forward(lbmhd_closure_t* c, const float* x, int batch, int h, int w, float* out,
+                          int tensor_cores);
+const char* lbmhd_closure_last_error(const lbmhd_closure_t* c);
+void lbmhd_closure_free(lbmhd_closure_t* c);
+/* Attach a closure to a square binary64 / binary32 handle (NULL detaches): every step then runs
+ * moments -> features -> network (tensor cores) -> correction -> fused step.  The closure must
+ * outlive the attachment and must not be trained while attached. */
+int lbmhd_set_closure(lbmhd_t* h, lbmhd_closure_t* c);
+
 /* Size in bytes of a checkpoint of this handle's state. */
 size_t lbmhd_state_bytes(const lbmhd_t* h);
 

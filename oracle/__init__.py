@@ -52,6 +52,9 @@ def _load():
             lib.oracle_step.argtypes = [ctypes.c_int, ctypes.c_int, _D, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_int, _D, _D, ctypes.c_int,
                                         ctypes.c_int]
+            lib.oracle_step_corrected.argtypes = [ctypes.c_int, ctypes.c_int, _D, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_int, _D, _D,
+                                                  ctypes.c_int, ctypes.c_int, _D]
             lib.oracle_collide_cell.argtypes = [ctypes.c_int, ctypes.c_int, _D, ctypes.c_double,
                                                 ctypes.c_double, ctypes.c_int, _D, _D,
                                                 ctypes.c_int, ctypes.c_int, _D, _D]
@@ -139,6 +142,19 @@ def step(f, g, s, s_m, delta, nsteps, stencil=0, nthreads=1):
     s = _arr(s, 9)
     _check(_load().oracle_step(nx, ny, _p(s), s_m, delta, stencil, _p(f), _p(g), nsteps,
                                nthreads), "step")
+    return f, g
+
+
+def step_corrected(f, g, s, s_m, delta, nsteps, corr, stencil=0, nthreads=1):
+    """``step`` with a fixed additive correction corr[4, ny, nx] of the four subgrid terms
+    (xy stress, normal-stress difference, trace, electric field) at every cell and step."""
+    f = np.array(f, dtype=np.float64, order="C", copy=True)
+    g = np.array(g, dtype=np.float64, order="C", copy=True)
+    ny, nx = f.shape[1:]
+    s = _arr(s, 9)
+    corr = _arr(corr, (4, ny, nx))
+    _check(_load().oracle_step_corrected(nx, ny, _p(s), s_m, delta, stencil, _p(f), _p(g), nsteps,
+                                         nthreads, _p(corr)), "step_corrected")
     return f, g
 
 

@@ -166,8 +166,19 @@ static double filt_ratio(double X, double Y, double Z, const double* gX, const d
  *   B_a B_b                 -> filt_prod(B_a, B_b)
  * J[a], B[a]: filtered J = rho u and B at the cell;  gJ[a][beta] = d_beta J_a,
  * gB[a][beta] = d_beta B_a;  kd = Delta^2/12.  Delta = 0 gives the table exactly. */
+static void meq_corrected(double rho, const double* J, const double* B, const double* gJ,
+                          const double* gB, double kd, const double* cq, double* M);
+
 void oracle_meq(double rho, const double* J, const double* B, const double* gJ,
                 const double* gB, double kd, double* M) {
+  meq_corrected(rho, J, B, gJ, gB, kd, NULL, M);
+}
+
+/* As oracle_meq, plus an optional additive correction cq[0..3] of the four subgrid terms:
+ * cq[0] is added to the xy stress (M_3), cq[1] to the normal-stress difference (M_4), cq[2] to
+ * the trace (J_x^2 + J_y^2)/rho that M_7 and M_8 carry with factor -3. */
+static void meq_corrected(double rho, const double* J, const double* B, const double* gJ,
+                          const double* gB, double kd, const double* cq, double* M) {
   const double* gJx = gJ;
   const double* gJy = gJ + 2;
   const double* gBx = gB;
@@ -187,18 +198,35 @@ void oracle_meq(double rho, const double* J, const double* B, const double* gJ,
   M[6] = -J[1];                                /* -rho u_y */
   M[7] = -3.0 * (JxJx + JyJy);                 /* -3((rho u_x)^2+(rho u_y)^2)/rho */
   M[8] = 5.0 / 3.0 * rho - 3.0 * (JxJx + JyJy); /* 5/3 rho - 3(...)/rho */
+  if (cq) {
+    M[3] += cq[0];
+    M[4] += cq[1];
+    M[7] -= 3.0 * cq[2];
+    M[8] -= 3.0 * cq[2];
+  }
 }
 
 /* ---- Eq. MagMomentEq with the Delta^2 terms ------------------------------------------
  * N^eq_{alpha q} as the printed table, with u = J/rho (R2), so each product
  * u_beta B_alpha = (rho u_beta) B_alpha / rho is filtered by Eq. FilterExampleLarge.
  * N[alpha*9 + q]. */
+static void neq_corrected(double rho, const double* J, const double* B, const double* gJ,
+                          const double* gB, double kd, const double* cq, double* N);
+
 void oracle_neq(double rho, const double* J, const double* B, const double* gJ,
                 const double* gB, double kd, double* N) {
+  neq_corrected(rho, J, B, gJ, gB, kd, NULL, N);
+}
+
+/* As oracle_neq, plus an optional correction cq[3] of the electric field
+ * E = P[x][y] - P[y][x] (added to P[x][y], so every N entry carrying E receives it). */
+static void neq_corrected(double rho, const double* J, const double* B, const double* gJ,
+                          const double* gB, double kd, const double* cq, double* N) {
   /* P[b][a] = filtered (rho u_b) B_a / rho */
   double P[2][2];
   for (int b = 0; b < 2; ++b)
     for (int a = 0; a < 2; ++a) P[b][a] = filt_ratio(J[b], B[a], rho, gJ + 2 * b, gB + 2 * a, kd);
+  if (cq) P[0][1] += cq[3];
   for (int a = 0; a < 2; ++a) {
     double* Na = N + 9 * a;
     Na[0] = B[a];                          /* N_a0 = B_a */
@@ -262,7 +290,7 @@ static void field_gradient(const double* a, int nx, int ny, int x, int y, int st
  *   f* = T^{-1} M*,  g*_a = T_m^{-1} N*_a.                                                */
 static void collide_cell(const double* fc, const double* gc, double rho, const double* J,
                          const double* B, const double* gJ, const double* gB, const double* s,
-                         double s_m, double kd, double* fstar, double* gstar) {
+                         double s_m, double kd, const double* cq, double* fstar, double* gstar) {
   double M[9], Meq[9], Ms[9], N[18], Neq[18], Ns[18];
   for (int j = 0; j < 9; ++j) {
     double acc = 0.0;
@@ -275,8 +303,8 @@ static void collide_cell(const double* fc, const double* gc, double rho, const d
       for (int i = 0; i < 9; ++i) acc += TMAG[j][i] * gc[9 * a + i];
       N[9 * a + j] = acc;
     }
-  oracle_meq(rho, J, B, gJ, gB, kd, Meq);
-  oracle_neq(rho, J, B, gJ, gB, kd, Neq);
+  meq_corrected(rho, J, B, gJ, gB, kd, cq, Meq);
+  neq_corrected(rho, J, B, gJ, gB, kd, cq, Neq);
   for (int j = 0; j < 9; ++j) Ms[j] = M[j] - s[j] * (M[j] - Meq[j]);
   for (int q = 0; q < 18; ++q) Ns[q] = N[q] - s_m * (N[q] - Neq[q]);
   for (int i = 0; i < 9; ++i) {
@@ -298,6 +326,7 @@ typedef struct {
   const double *f, *g, *rho, *jx, *jy, *bx, *by, *s;
   double s_m, kd;
   double *fs, *gs;
+  const double* corr; /* optional correction planes [4][ny][nx] */
 } row_job;
 
 static void gather_cell(const double* f, const double* g, size_t ncell, size_t c, double* fc,
@@ -325,7 +354,11 @@ static void* collide_rows(void* arg) {
       field_gradient(jb->jy, jb->nx, jb->ny, x, y, jb->stencil, gJ + 2);
       field_gradient(jb->bx, jb->nx, jb->ny, x, y, jb->stencil, gB);
       field_gradient(jb->by, jb->nx, jb->ny, x, y, jb->stencil, gB + 2);
-      collide_cell(fc, gc, jb->rho[c], J, B, gJ, gB, jb->s, jb->s_m, jb->kd, fst, gst);
+      double cq[4];
+      if (jb->corr)
+        for (int q = 0; q < 4; ++q) cq[q] = jb->corr[(size_t)q * ncell + c];
+      collide_cell(fc, gc, jb->rho[c], J, B, gJ, gB, jb->s, jb->s_m, jb->kd, jb->corr ? cq : NULL,
+                   fst, gst);
       for (int i = 0; i < 9; ++i) {
         jb->fs[(size_t)i * ncell + c] = fst[i];
         jb->gs[(size_t)i * ncell + c] = gst[i];
@@ -354,8 +387,24 @@ static int check_args(int nx, int ny, const double* s, double s_m, double delta,
  * s[9]: fluid rates in the order of the rows of T (s[0..2] act on conserved moments and do
  * not change the result); s_m: magnetic rate; delta: filter width (kd = delta^2/12).
  * Returns 0, or -1 on invalid arguments, -3 if memory runs out. */
+static int step_impl(int nx, int ny, const double* s, double s_m, double delta, int stencil,
+                     double* f, double* g, int nsteps, int nthreads, const double* corr);
+
 int oracle_step(int nx, int ny, const double* s, double s_m, double delta, int stencil,
                 double* f, double* g, int nsteps, int nthreads) {
+  return step_impl(nx, ny, s, s_m, delta, stencil, f, g, nsteps, nthreads, NULL);
+}
+
+/* oracle_step with a fixed additive correction of the four subgrid terms at every cell and
+ * step: corr[4][ny][nx] = (xy stress, normal-stress difference, trace, electric field). */
+int oracle_step_corrected(int nx, int ny, const double* s, double s_m, double delta, int stencil,
+                          double* f, double* g, int nsteps, int nthreads, const double* corr) {
+  if (!corr) return -1;
+  return step_impl(nx, ny, s, s_m, delta, stencil, f, g, nsteps, nthreads, corr);
+}
+
+static int step_impl(int nx, int ny, const double* s, double s_m, double delta, int stencil,
+                     double* f, double* g, int nsteps, int nthreads, const double* corr) {
   if (check_args(nx, ny, s, s_m, delta, stencil) || !f || !g || nsteps < 0) return -1;
   if (!ensure_inverses()) return -1;
   if (nthreads < 1) nthreads = 1;
@@ -389,7 +438,7 @@ int oracle_step(int nx, int ny, const double* s, double s_m, double delta, int s
     /* 2 + 3. gradients and collision, rows split over threads */
     for (int t = 0; t < nthreads; ++t) {
       row_job jb = {nx, ny, (int)((long)ny * t / nthreads), (int)((long)ny * (t + 1) / nthreads),
-                    stencil, f, g, rho, jx, jy, bx, by, s, s_m, kd, fs, gs};
+                    stencil, f, g, rho, jx, jy, bx, by, s, s_m, kd, fs, gs, corr};
       jobs[t] = jb;
     }
     if (nthreads == 1) {
@@ -466,7 +515,7 @@ int oracle_collide_cell(int nx, int ny, const double* s, double s_m, double delt
   double J[2] = {nb[1][1][1], nb[2][1][1]}, B[2] = {nb[3][1][1], nb[4][1][1]};
   double gJ[4] = {grad[0][0], grad[0][1], grad[1][0], grad[1][1]};
   double gB[4] = {grad[2][0], grad[2][1], grad[3][0], grad[3][1]};
-  collide_cell(fc, gc, nb[0][1][1], J, B, gJ, gB, s, s_m, delta * delta / 12.0, fstar, gstar);
+  collide_cell(fc, gc, nb[0][1][1], J, B, gJ, gB, s, s_m, delta * delta / 12.0, NULL, fstar, gstar);
   return 0;
 }
 

@@ -88,6 +88,7 @@ void free_all(lbmhd_t* h) {
   if (h->diag_out) cudaFree(h->diag_out);
   if (h->err_flag) cudaFree(h->err_flag);
   if (h->spec_work) cudaFree(h->spec_work);
+  if (h->cl_buf) cudaFree(h->cl_buf);
   if (h->ev_a) cudaEventDestroy(h->ev_a);
   if (h->ev_b) cudaEventDestroy(h->ev_b);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -224,19 +225,49 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
   return LBMHD_OK;
 }
 
-// One fused step from copy `from` into copy `to`.
-cudaError_t launch_one(lbmhd_t* h, int from, int to) {
+// One fused step from copy `from` into copy `to` (with the subgrid correction planes `corr`,
+// or none).
+cudaError_t launch_one(lbmhd_t* h, int from, int to, const float* corr = nullptr) {
   switch (h->precision) {
     case LBMHD_FP64:
       return launch_step_f64(h->tmap[from], (double*)h->pops[to], h->geom, h->coef,
-                             h->p.grad_stencil, h->err_flag, h->stream);
+                             h->p.grad_stencil, h->err_flag, corr, h->stream);
     case LBMHD_FP32:
       return launch_step_f32(h->tmap[from], (float*)h->pops[to], h->geom, h->coef,
-                             h->p.grad_stencil, h->err_flag, h->stream);
+                             h->p.grad_stencil, h->err_flag, corr, h->stream);
     default:
       return launch_step_f16(h->tmap[from], (__half*)h->pops[to], h->geom, h->coef,
-                             h->p.grad_stencil, h->err_flag, h->stream);
+                             h->p.grad_stencil, h->err_flag, corr, h->stream);
   }
+}
+
+// One step with the attached correction: the caller's static planes, or the learned closure's
+// output for the current state (moments -> features -> network -> correction -> step).
+int one_step_corrected(lbmhd_t* h) {
+  const float* corr = h->corr_static;
+  if (h->closure) {
+    const int m = h->p.nx;
+    const size_t mm = (size_t)m * m;
+    double* f = h->fields;
+    LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, f, f + mm, f + 2 * mm, f + 3 * mm,
+                              f + 4 * mm, h->stream));
+    const float* sc = closure_device_scales(h->closure);
+    float* feat = h->cl_buf;
+    float* a1 = feat + 12 * mm;
+    float* a2 = a1 + 32 * mm;
+    float* c = a2 + 32 * mm;
+    LB_CUDA(h, closure_correction(closure_device_params(h->closure), sc, sc + 12, f, m, feat, a1, a2, c,
+                                  h->stream));
+    h->launches += 6;
+    corr = c;
+  }
+  const int nxt = h->cur ^ 1;
+  cudaError_t e = launch_one(h, h->cur, nxt, corr);
+  if (e != cudaSuccess) return cuda_fail(h, e, "fused step launch (corrected)");
+  h->cur = nxt;
+  h->launches += 1;
+  h->steps += 1;
+  return LBMHD_OK;
 }
 
 int build_graph(lbmhd_t* h, int parity) {
@@ -377,6 +408,13 @@ int lbmhd_step(lbmhd_t* h, int nsteps) {
     return fail(h, LBMHD_ERR_INVALID, "this handle is an ensemble member: step the ensemble");
   if (nsteps < 0) return fail(h, LBMHD_ERR_INVALID, "nsteps = %d < 0", nsteps);
   int n = nsteps;
+  if (h->corr_static || h->closure) {
+    for (; n > 0; --n) {
+      int rc = one_step_corrected(h);
+      if (rc) return rc;
+    }
+    return LBMHD_OK;
+  }
   // whole graphs of kGraphSteps launches when the handle owns its stream
   if (h->own_stream && n >= kGraphSteps) {
     if (!h->graph[h->cur]) {
@@ -485,6 +523,33 @@ int lbmhd_energy_spectrum(lbmhd_t* h, int nbins, double* e_kin, double* e_mag) {
   LB_CUDA(h, cudaMemcpyAsync(e_mag, dm, nbins * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LB_CUDA(h, cudaStreamSynchronize(h->stream));
   return check_step_status(h);
+}
+
+int lbmhd_set_correction_device(lbmhd_t* h, const float* corr) {
+  if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (corr && h->precision == LBMHD_FP16)
+    return fail(h, LBMHD_ERR_INVALID, "the subgrid correction needs binary64 or binary32 storage");
+  if (corr && h->closure) return fail(h, LBMHD_ERR_INVALID, "detach the learned closure first");
+  h->corr_static = corr;
+  return LBMHD_OK;
+}
+
+int lbmhd_set_closure(lbmhd_t* h, lbmhd_closure_t* c) {
+  if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (c) {
+    if (h->precision == LBMHD_FP16)
+      return fail(h, LBMHD_ERR_INVALID, "the learned closure needs binary64 or binary32 storage");
+    if (h->p.nx != h->p.ny) return fail(h, LBMHD_ERR_INVALID, "the learned closure needs a square grid");
+    if (h->corr_static) return fail(h, LBMHD_ERR_INVALID, "detach the static correction first");
+    if (!h->cl_buf) {
+      const size_t mm = (size_t)h->p.nx * h->p.ny;
+      LB_CUDA(h, cudaMalloc(&h->cl_buf, (12 + 32 + 32 + 4) * mm * sizeof(float)));
+    }
+    // the closure's parameters must be in place before this handle's stream reads them
+    LB_CUDA(h, cudaStreamSynchronize(closure_stream(c)));
+  }
+  h->closure = c;
+  return LBMHD_OK;
 }
 
 size_t lbmhd_state_bytes(const lbmhd_t* h) { return h ? h->state_bytes : 0; }

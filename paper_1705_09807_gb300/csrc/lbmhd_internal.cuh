@@ -20,6 +20,8 @@
 
 #include <cuda.h>
 #include <cuda_fp16.h>
+
+#include "lbmhd.h"
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -86,13 +88,18 @@ struct StepGeom {
 
 // Fused step launchers (lbmhd_step.cu).  `src` is a 3-D tensor map {pitch, ny, 27} of the
 // source copy (box {box_width(elem), 1, 9}); dst is the other copy.  *err receives 1 if a pipeline wait
-// timed out (the kernel then stops early; the state is not valid).
+// timed out (the kernel then stops early; the state is not valid).  corr (may be NULL): four
+// binary32 planes [4][ny][nx] added to the subgrid terms of the collision (xy stress, normal
+// stress difference, trace, electric field); not offered for binary16 storage.
 cudaError_t launch_step_f64(const CUtensorMap& src, double* dst, const StepGeom& g,
-                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s);
+                            const StepCoef& c, int stencil, unsigned* err, const float* corr,
+                            cudaStream_t s);
 cudaError_t launch_step_f32(const CUtensorMap& src, float* dst, const StepGeom& g,
-                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s);
+                            const StepCoef& c, int stencil, unsigned* err, const float* corr,
+                            cudaStream_t s);
 cudaError_t launch_step_f16(const CUtensorMap& src, __half* dst, const StepGeom& g,
-                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s);
+                            const StepCoef& c, int stencil, unsigned* err, const float* corr,
+                            cudaStream_t s);
 // Rows per block for the grid and precision (one wave of resident blocks when possible).
 int step_band_rows(int nx, int ny, int precision, int num_sms);
 // Opt the step kernels in to their dynamic shared memory (once per process and device).
@@ -134,6 +141,18 @@ size_t spectrum_work_bytes(int n);
 cudaError_t launch_energy_spectrum(const double* ux, const double* uy, const double* bx,
                                    const double* by, int n, int nbins, double* ek, double* em,
                                    void* work, cudaStream_t s);
+
+// Learned closure (lbmhd_closure.cu): correction planes [4][m][m] for a square coarse state
+// given as binary64 planes (rho, ux, uy, bx, by), via features and the bf16 tensor-core network.
+// feat: 12 m^2 floats; a1, a2: 32 m^2 floats each; corr: 4 m^2 floats.
+int closure_num_params();
+cudaError_t closure_correction(const float* params, const float* in_scale, const float* out_scale,
+                               const double* state, int m, float* feat, float* a1, float* a2,
+                               float* corr, cudaStream_t s);
+
+const float* closure_device_params(const lbmhd_closure_t* c);
+const float* closure_device_scales(const lbmhd_closure_t* c);
+cudaStream_t closure_stream(const lbmhd_closure_t* c);
 
 // Store a message for lbmhd_last_error(NULL) on the calling thread (lbmhd_api.cu).
 void set_thread_error(const char* msg);

@@ -51,9 +51,9 @@ struct KCoef {
 // Collision of one cell; p[] holds the pulled (current) populations with f as deviations
 // f_i - w_i, and receives the post-collision values.  rho1 = rho - 1.  dJ = undivided
 // differences {dx Jx, dy Jx, dx Jy, dy Jy}, dB likewise; c.kq folds in their scale.
-template <typename T>
+template <typename T, bool CORR = false>
 __device__ __forceinline__ void collide(T p[kQ], T rho1, T jx, T jy, T bx, T by, const T dJ[4],
-                                        const T dB[4], const KCoef<T>& c) {
+                                        const T dB[4], const KCoef<T>& c, const T* cq = nullptr) {
   const T ir = T(1) / (T(1) + rho1);
   const T k = c.kq;
   // gradient products
@@ -72,13 +72,23 @@ __device__ __forceinline__ void collide(T p[kQ], T rho1, T jx, T jy, T bx, T by,
   const T Rxx = bx * bx + k * Hxx;
   const T Ryy = by * by + k * Hyy;
   const T Rxy = bx * by + k * Hxy;
-  const T E = (jx * by - jy * bx + k * (Kxy - Kyx)) * ir;
+  T E = (jx * by - jy * bx + k * (Kxy - Kyx)) * ir;
+  // optional additive correction of the four subgrid terms (xy stress, normal-stress
+  // difference, trace, electric field), e.g. from the learned closure
+  T c0 = T(0), c1 = T(0), c2 = T(0);
+  if (CORR) {
+    c0 = cq[0];
+    c1 = cq[1];
+    c2 = cq[2];
+    E += cq[3];
+  }
 
   // ---- fluid: non-equilibrium parts of moments 3..8 (rows of Eq. FluidTMatrix) ----
   const T a13 = p[1] + p[3], a24 = p[2] + p[4], a57 = p[5] + p[7], a68 = p[6] + p[8];
-  const T qq = Qxx + Qyy;
-  const T n3 = (a57 - a68) - (Qxy - Rxy);
-  const T n4 = (a13 - a24) - ((Qxx - Qyy) - (Rxx - Ryy));
+  const T qq = CORR ? (Qxx + Qyy) + c2 : Qxx + Qyy;
+  const T n3 = CORR ? (a57 - a68) - ((Qxy - Rxy) + c0) : (a57 - a68) - (Qxy - Rxy);
+  const T n4 = CORR ? (a13 - a24) - (((Qxx - Qyy) - (Rxx - Ryy)) + c1)
+                    : (a13 - a24) - ((Qxx - Qyy) - (Rxx - Ryy));
   const T n5 = T(2) * (p[3] - p[1]) + ((p[5] - p[6]) + (p[8] - p[7])) + jx;
   const T n6 = T(2) * (p[4] - p[2]) + ((p[5] - p[8]) + (p[6] - p[7])) + jy;
   const T n7 = T(4) * p[0] - T(5) * (a13 + a24) + T(4) * (a57 + a68) + T(3) * qq;
@@ -198,10 +208,11 @@ __device__ __forceinline__ void init_stage_barriers(StepSmem<S, NST>& S_, const 
 // of one grid, marched in direction +1 (band_parity even) or -1 (odd).  `kbase` counts the rows
 // this block has staged before this tile, so stage slots and mbarrier phases continue across
 // tiles.  Returns false if a wait timed out (the block must stop; *err is set).
-template <typename S, int ISO, int NST>
+template <typename S, int ISO, int NST, bool CORR = false>
 __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict__ dst, const StepGeom& g,
                                          const KCoef<typename ArithOf<S>::type>& c, int x0, int y0,
-                                         int band_parity, uint32_t& kbase, unsigned* __restrict__ err) {
+                                         int band_parity, uint32_t& kbase, unsigned* __restrict__ err,
+                                         const float* __restrict__ corr = nullptr) {
   using SM = StepSmem<S, NST>;
   using T = typename SM::C;
   constexpr int GE = SM::kGroupElems;
@@ -344,9 +355,16 @@ __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict_
       T p[kQ];
 #pragma unroll
       for (int q = 0; q < kQ; ++q) p[q] = staged<T, S, BW>(st, GE, q, t + LEAD);
-      collide(p, rho_cur, jx, jy, bx, by, dJ, dB, c);
       const int y = row_of(m);
       const int x = x0 + t;
+      if (CORR) {
+        const size_t cell = (size_t)y * nx + x, cplane = (size_t)nx * ny;
+        const T cq[4] = {(T)corr[cell], (T)corr[cplane + cell], (T)corr[2 * cplane + cell],
+                         (T)corr[3 * cplane + cell]};
+        collide<T, true>(p, rho_cur, jx, jy, bx, by, dJ, dB, c, cq);
+      } else {
+        collide(p, rho_cur, jx, jy, bx, by, dJ, dB, c);
+      }
       S* o = dst + (size_t)y * pitch + kXOff + x;
 #pragma unroll
       for (int q = 0; q < kQ; ++q) o[(size_t)plane_of(q) * g.plane] = store_as<S>(p[q]);
@@ -365,16 +383,17 @@ __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict_
   return true;
 }
 
-// One grid: block (strip, band) = one tile.
-template <typename S, int ISO, int NST, int MINB>
+// One grid: block (strip, band) = one tile.  CORR: add the correction planes corr[4][ny][nx].
+template <typename S, int ISO, int NST, int MINB, bool CORR = false>
 __global__ void __launch_bounds__(kStepThreads, MINB)
     fused_step_kernel(const __grid_constant__ CUtensorMap src, S* __restrict__ dst, StepGeom g,
-                      KCoef<typename ArithOf<S>::type> c, unsigned* __restrict__ err) {
+                      KCoef<typename ArithOf<S>::type> c, unsigned* __restrict__ err,
+                      const float* __restrict__ corr) {
   if ((int)blockIdx.y * g.band >= g.ny) return;  // uniform per block
   init_stage_barriers(step_smem<S, NST>(), &src);
   uint32_t kbase = 0;
-  run_tile<S, ISO, NST>(&src, dst, g, c, blockIdx.x * kStepThreads, blockIdx.y * g.band, blockIdx.y,
-                        kbase, err);
+  run_tile<S, ISO, NST, CORR>(&src, dst, g, c, blockIdx.x * kStepThreads, blockIdx.y * g.band,
+                              blockIdx.y, kbase, err, corr);
 }
 
 // Ensemble: every member grid advances one step in this launch.  work[i] = {member, x0, y0,
@@ -471,9 +490,9 @@ template <> struct StepConfig<__half> {
   static constexpr int kStages = LBMHD_F16_STAGES, kMinBlocks = LBMHD_F16_BLOCKS;
 };
 
-template <typename S, int ISO>
+template <typename S, int ISO, bool CORR = false>
 constexpr auto kernel_ptr() {
-  return &fused_step_kernel<S, ISO, StepConfig<S>::kStages, StepConfig<S>::kMinBlocks>;
+  return &fused_step_kernel<S, ISO, StepConfig<S>::kStages, StepConfig<S>::kMinBlocks, CORR>;
 }
 
 template <typename S>
@@ -483,13 +502,22 @@ constexpr size_t smem_bytes() {
 
 template <typename S>
 cudaError_t launch_step(const CUtensorMap& src, S* dst, const StepGeom& g, const StepCoef& c,
-                        int stencil, unsigned* err, cudaStream_t s) {
+                        int stencil, unsigned* err, const float* corr, cudaStream_t s) {
   dim3 grid((g.nx + kStepThreads - 1) / kStepThreads, (g.ny + g.band - 1) / g.band);
   auto k = cast_coef<typename ArithOf<S>::type>(c);
-  if (stencil == 1)
-    kernel_ptr<S, 1>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(src, dst, g, k, err);
-  else
-    kernel_ptr<S, 0>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(src, dst, g, k, err);
+  if (corr) {
+    if constexpr (sizeof(S) == 2) {
+      return cudaErrorNotSupported;  // the correction is offered for binary64 / binary32 storage
+    } else if (stencil == 1) {
+      kernel_ptr<S, 1, true>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(src, dst, g, k, err, corr);
+    } else {
+      kernel_ptr<S, 0, true>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(src, dst, g, k, err, corr);
+    }
+  } else if (stencil == 1) {
+    kernel_ptr<S, 1>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(src, dst, g, k, err, nullptr);
+  } else {
+    kernel_ptr<S, 0>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(src, dst, g, k, err, nullptr);
+  }
   return cudaGetLastError();
 }
 
@@ -504,6 +532,12 @@ cudaError_t set_smem_attr() {
   cudaError_t e = cudaFuncSetAttribute(kernel_ptr<S, 0>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kernel_ptr<S, 1>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if constexpr (sizeof(S) != 2) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kernel_ptr<S, 0, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kernel_ptr<S, 1, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  }
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(ensemble_kernel_ptr<S, 0>(), cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
@@ -546,18 +580,21 @@ cudaError_t prepare_step_kernels() {
 }
 
 cudaError_t launch_step_f64(const CUtensorMap& src, double* dst, const StepGeom& g,
-                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s) {
-  return launch_step<double>(src, dst, g, c, stencil, err, s);
+                            const StepCoef& c, int stencil, unsigned* err, const float* corr,
+                            cudaStream_t s) {
+  return launch_step<double>(src, dst, g, c, stencil, err, corr, s);
 }
 
 cudaError_t launch_step_f32(const CUtensorMap& src, float* dst, const StepGeom& g,
-                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s) {
-  return launch_step<float>(src, dst, g, c, stencil, err, s);
+                            const StepCoef& c, int stencil, unsigned* err, const float* corr,
+                            cudaStream_t s) {
+  return launch_step<float>(src, dst, g, c, stencil, err, corr, s);
 }
 
 cudaError_t launch_step_f16(const CUtensorMap& src, __half* dst, const StepGeom& g,
-                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s) {
-  return launch_step<__half>(src, dst, g, c, stencil, err, s);
+                            const StepCoef& c, int stencil, unsigned* err, const float* corr,
+                            cudaStream_t s) {
+  return launch_step<__half>(src, dst, g, c, stencil, err, corr, s);
 }
 
 size_t ensemble_member_bytes(int precision) {

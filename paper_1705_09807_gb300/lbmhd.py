@@ -58,6 +58,7 @@ class LbmhdUnstable(LbmhdError):
 _lib = None
 _lock = threading.Lock()
 _D = ctypes.POINTER(ctypes.c_double)
+_F = ctypes.POINTER(ctypes.c_float)
 _H = ctypes.c_void_p
 
 
@@ -110,6 +111,25 @@ def load_library(path: str | None = None):
             "lbmhd_ensemble_launch_count": (ctypes.c_uint64, [_H]),
             "lbmhd_ensemble_last_error": (ctypes.c_char_p, [_H]),
             "lbmhd_ensemble_free": (None, [_H]),
+            "lbmhd_set_correction_device": (ctypes.c_int, [_H, ctypes.c_void_p]),
+            "lbmhd_set_closure": (ctypes.c_int, [_H, ctypes.c_void_p]),
+            "lbmhd_closure_num_params": (ctypes.c_int, []),
+            "lbmhd_closure_create": (ctypes.c_int, [ctypes.POINTER(_H), _F, _F, _F]),
+            "lbmhd_closure_get_params": (ctypes.c_int, [_H, _F]),
+            "lbmhd_closure_set_params": (ctypes.c_int, [_H, _F]),
+            "lbmhd_closure_training_pair": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                           ctypes.c_double, ctypes.c_void_p,
+                                                           ctypes.c_void_p, ctypes.c_void_p]),
+            "lbmhd_closure_features": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                                      ctypes.c_void_p, ctypes.c_void_p]),
+            "lbmhd_closure_gradient": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                      ctypes.c_int, ctypes.c_int, _F, _D]),
+            "lbmhd_closure_train_step": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                        ctypes.c_int, ctypes.c_int, ctypes.c_float, _D]),
+            "lbmhd_closure_forward": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+            "lbmhd_closure_last_error": (ctypes.c_char_p, [_H]),
+            "lbmhd_closure_free": (None, [_H]),
             "lbmhd_step_count": (ctypes.c_int64, [_H]),
             "lbmhd_last_error": (ctypes.c_char_p, [_H]),
             "lbmhd_free": (None, [_H]),
@@ -451,3 +471,121 @@ class Ensemble:
             self.free()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- subgrid correction, closure
+def lbmhd_set_correction_device(h, corr) -> None:
+    """Static correction planes: CUDA float32 tensor [4, ny, nx] (kept alive by the caller), or
+    None to detach."""
+    ptr = None
+    if corr is not None:
+        import torch
+        if not (corr.is_cuda and corr.dtype == torch.float32 and corr.is_contiguous()):
+            raise ValueError("expected a contiguous CUDA float32 tensor [4, ny, nx]")
+        ptr = corr.data_ptr()
+    _check(load_library().lbmhd_set_correction_device(h, ptr), h)
+
+
+def _f32(a, n=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values")
+    return a
+
+
+class Closure:
+    """The learned subgrid correction network (lbmhd_closure_* in the C ABI)."""
+
+    def __init__(self, params, in_scale, out_scale):
+        lib = load_library()
+        self.n_params = int(lib.lbmhd_closure_num_params())
+        p = _f32(params, self.n_params)
+        i = _f32(in_scale, 12)
+        o = _f32(out_scale, 4)
+        self.h = _H()
+        rc = lib.lbmhd_closure_create(ctypes.byref(self.h), p.ctypes.data_as(_F), i.ctypes.data_as(_F),
+                                      o.ctypes.data_as(_F))
+        if rc != LBMHD_OK:
+            raise LbmhdError(rc, (lib.lbmhd_closure_last_error(None) or b"").decode())
+        self.in_scale, self.out_scale = i, o
+
+    def _check(self, rc):
+        if rc != LBMHD_OK:
+            raise LbmhdError(rc, (load_library().lbmhd_closure_last_error(self.h) or b"").decode())
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        self._check(load_library().lbmhd_closure_get_params(self.h, out.ctypes.data_as(_F)))
+        return out
+
+    def set_params(self, params) -> None:
+        p = _f32(params, self.n_params)
+        self._check(load_library().lbmhd_closure_set_params(self.h, p.ctypes.data_as(_F)))
+
+    def training_pair(self, fine, r, delta, x, t, work) -> None:
+        """fine: CUDA float64 [5, n, n] (rho, ux, uy, bx, by); x [12, m, m], t [4, m, m] float32;
+        work: CUDA float64 with at least 9 m^2 elements."""
+        n = fine.shape[-1]
+        m = n // r
+        self._check(load_library().lbmhd_closure_training_pair(
+            self.h, _dptr(fine, 5 * n * n), n, r, delta, _dptr32(x, 12 * m * m), _dptr32(t, 4 * m * m),
+            _dptr(work, work.numel()) if work.numel() >= 9 * m * m else None))
+
+    def features(self, state, delta, x, analytic=None) -> None:
+        m = state.shape[-1]
+        self._check(load_library().lbmhd_closure_features(
+            self.h, _dptr(state, 5 * m * m), m, delta, _dptr32(x, 12 * m * m),
+            None if analytic is None else _dptr32(analytic, 4 * m * m)))
+
+    def gradient(self, x, t):
+        b, _, hh, ww = x.shape
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(load_library().lbmhd_closure_gradient(
+            self.h, _dptr32(x, x.numel()), _dptr32(t, t.numel()), b, hh, ww, g.ctypes.data_as(_F),
+            ctypes.byref(loss)))
+        return loss.value, g
+
+    def train_step(self, x, t, lr: float) -> float:
+        b, _, hh, ww = x.shape
+        loss = ctypes.c_double()
+        self._check(load_library().lbmhd_closure_train_step(
+            self.h, _dptr32(x, x.numel()), _dptr32(t, t.numel()), b, hh, ww, float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def forward(self, x, out, tensor_cores: bool = True) -> None:
+        b, _, hh, ww = x.shape
+        self._check(load_library().lbmhd_closure_forward(
+            self.h, _dptr32(x, x.numel()), b, hh, ww, _dptr32(out, out.numel()), int(tensor_cores)))
+
+    def attach(self, h) -> None:
+        _check(load_library().lbmhd_set_closure(h, self.h), h)
+
+    def free(self):
+        if self.h is not None and self.h.value:
+            load_library().lbmhd_closure_free(self.h)
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def lbmhd_detach_closure(h) -> None:
+    _check(load_library().lbmhd_set_closure(h, None), h)
+
+
+def _dptr32(t, n: int) -> int:
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous() and t.numel() == n):
+        raise ValueError("expected a contiguous CUDA float32 tensor of matching size")
+    return t.data_ptr()

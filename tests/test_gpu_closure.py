@@ -1,0 +1,154 @@
+"""The learned closure on the GPU against the FP64 oracle (oracle/closure.py): back-propagation,
+the binary32 and bf16 tensor-core forward passes, features and training targets from a fine
+state, the correction inside the fused step (against the oracle's corrected step), and the
+closure-in-the-loop step against the same correction supplied statically."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closure as oc
+from paper_1705_09807_gb300 import lbmhd
+from paper_1705_09807_gb300.inputs import kh_jet, smooth_random_fields, splitmix64_uniform
+
+pytestmark = pytest.mark.gpu
+IN_SCALE = np.array([0.05, 0.05, 0.03, 0.03] + [0.005] * 8, dtype=np.float32)
+OUT_SCALE = np.array([1e-6, 1e-6, 1e-6, 1e-6], dtype=np.float32)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1705_09807_gb300 import build
+    build.build()
+    lbmhd.load_library()
+
+
+def _params(seed=3):
+    u = splitmix64_uniform(seed, oc.num_params())
+    theta = oc.init_params(seed) + 0.02 * (2 * u - 1)
+    return theta
+
+
+def _batch(b=2, h=12, w=20, seed=5):
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(b, 12, h, w)), 0.3 * rng.normal(size=(b, 4, h, w))
+
+
+def test_gradient_matches_oracle():
+    import torch
+    theta = _params()
+    x, t = _batch()
+    with lbmhd.Closure(theta, IN_SCALE, OUT_SCALE) as cl:
+        loss, g = cl.gradient(torch.tensor(x, dtype=torch.float32, device="cuda"),
+                              torch.tensor(t, dtype=torch.float32, device="cuda"))
+    th32 = theta.astype(np.float32).astype(np.float64)
+    L, gref = oc.gradient(th32, x.astype(np.float32).astype(np.float64),
+                          t.astype(np.float32).astype(np.float64))
+    assert abs(loss - L) < 1e-5 * L
+    err = np.linalg.norm(g - gref) / np.linalg.norm(gref)
+    assert err < 1e-5, err
+
+
+def test_forward_binary32_and_tensor_cores():
+    import torch
+    theta = _params(7)
+    x, _ = _batch(b=3, h=16, w=37, seed=9)  # width not a multiple of 16: ragged mma tiles
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    ref = oc.forward(theta.astype(np.float32).astype(np.float64), x.astype(np.float32).astype(np.float64))[-1]
+    with lbmhd.Closure(theta, IN_SCALE, OUT_SCALE) as cl:
+        out32 = torch.empty((3, 4, 16, 37), dtype=torch.float32, device="cuda")
+        cl.forward(xt, out32, tensor_cores=False)
+        out16 = torch.empty_like(out32)
+        cl.forward(xt, out16, tensor_cores=True)
+    o32, o16 = out32.cpu().numpy(), out16.cpu().numpy()
+    scale = np.sqrt(np.mean(ref ** 2))
+    assert np.max(np.abs(o32 - ref)) < 1e-5 * max(1.0, np.max(np.abs(ref)))
+    # bf16 operands (8-bit significand), binary32 accumulation over up to 288 terms
+    assert np.sqrt(np.mean((o16 - ref) ** 2)) < 2e-2 * scale
+
+
+def test_training_pair_and_features_match_oracle():
+    import torch
+    n, r, delta = 64, 4, 2.0
+    f = smooth_random_fields(n, n, seed=21, amp_u=0.05, amp_b=0.04, amp_rho=0.02, kmax=8)
+    fine = torch.tensor(np.stack(f), device="cuda")
+    m = n // r
+    x = torch.empty((12, m, m), dtype=torch.float32, device="cuda")
+    t = torch.empty((4, m, m), dtype=torch.float32, device="cuda")
+    work = torch.empty(9 * m * m, dtype=torch.float64, device="cuda")
+    with lbmhd.Closure(_params(), IN_SCALE, OUT_SCALE) as cl:
+        cl.training_pair(fine, r, delta, x, t, work)
+        xr, tr = oc.training_pair(*f, r, delta, IN_SCALE, OUT_SCALE)
+        np.testing.assert_allclose(x.cpu().numpy(), xr, rtol=2e-6, atol=1e-6)
+        np.testing.assert_allclose(t.cpu().numpy(), tr, rtol=1e-4, atol=1e-4 * np.max(np.abs(tr)))
+        # features of a coarse state given as rho, u, B planes
+        st = [oc.box(a, r) for a in (f[0], f[0] * f[1], f[0] * f[2], f[3], f[4])]
+        R = st[0]
+        state = torch.tensor(np.stack([R, st[1] / R, st[2] / R, st[3], st[4]]), device="cuda")
+        x2 = torch.empty_like(x)
+        an = torch.empty((4, m, m), dtype=torch.float32, device="cuda")
+        cl.features(state, delta, x2, an)
+        np.testing.assert_allclose(x2.cpu().numpy(), xr, rtol=2e-6, atol=1e-6)
+        ar = oc.analytic(R, st[1], st[2], st[3], st[4], delta)
+        np.testing.assert_allclose(an.cpu().numpy(), ar, rtol=1e-5, atol=1e-6 * np.max(np.abs(ar)))
+
+
+@pytest.mark.parametrize("precision,tol", [(lbmhd.LBMHD_FP64, 1e-13), (lbmhd.LBMHD_FP32, 2e-7)])
+def test_static_correction_matches_oracle(precision, tol):
+    import torch
+    nx, ny = 96, 40
+    f = smooth_random_fields(nx, ny, seed=2, amp_u=0.05, amp_b=0.04, amp_rho=0.02)
+    corr = (1e-4 * np.random.default_rng(3).normal(size=(4, ny, nx))).astype(np.float32)
+    s, sm = oracle.srt_rates(0.01), oracle.rate_from_diffusivity(0.01)
+    fo, go = oracle.init(*f)
+    fo, go = oracle.step_corrected(fo, go, s, sm, 2.0, 7, corr.astype(np.float64))
+    ref = np.concatenate([fo, go.reshape(18, ny, nx)])
+    ct = torch.tensor(corr, device="cuda")
+    with lbmhd.Lbmhd(lbmhd.make_params(nx, ny, s, sm, 2.0, precision), *f) as sim:
+        lbmhd.lbmhd_set_correction_device(sim.h, ct)
+        sim.step(7)
+        pops = sim.populations()
+    assert np.max(np.abs(pops - ref)) < tol
+    # and the correction really acts
+    fp, gp = oracle.step(*oracle.init(*f), s, sm, 2.0, 7)
+    assert np.max(np.abs(np.concatenate([fp, gp.reshape(18, ny, nx)]) - ref)) > 1e-6
+
+
+def test_closure_in_the_loop_equals_its_static_correction():
+    import torch
+    n = 64
+    f = kh_jet(n, seed=5)
+    s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
+    p = lbmhd.make_params(n, n, s, sm, 2.0, lbmhd.LBMHD_FP32)
+    with lbmhd.Closure(_params(), IN_SCALE, OUT_SCALE) as cl, \
+            lbmhd.Lbmhd(p, *f) as a, lbmhd.Lbmhd(p, *f) as b:
+        cl.attach(a.h)
+        a.step(1)
+        # the same correction by hand: moments -> features -> tensor-core network -> scale
+        st = [torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(5)]
+        b.moments_device(st)
+        torch.cuda.synchronize()
+        x = torch.empty((1, 12, n, n), dtype=torch.float32, device="cuda")
+        cl.features(torch.stack(st), 0.0, x.view(12, n, n))
+        out = torch.empty((1, 4, n, n), dtype=torch.float32, device="cuda")
+        cl.forward(x, out, tensor_cores=True)
+        corr = (out[0] * torch.tensor(OUT_SCALE, device="cuda")[:, None, None]).contiguous()
+        lbmhd.lbmhd_set_correction_device(b.h, corr)
+        b.step(1)
+        assert np.array_equal(a.populations(), b.populations())
+        lbmhd.lbmhd_detach_closure(a.h)
+        a.step(2)  # back to the analytic closure alone
+
+
+def test_training_lowers_the_loss():
+    import torch
+    x, t = _batch(b=2, h=16, w=16, seed=12)
+    t = 0.5 * np.tanh(x[:, :4])  # a learnable map
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    tt = torch.tensor(t, dtype=torch.float32, device="cuda")
+    with lbmhd.Closure(_params(), IN_SCALE, OUT_SCALE) as cl:
+        l0 = cl.train_step(xt, tt, 3e-3)
+        for _ in range(150):
+            l1 = cl.train_step(xt, tt, 3e-3)
+    assert l1 < 0.3 * l0
