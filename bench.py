@@ -358,9 +358,35 @@ def side_measurements(n, a):
     res["precision_rel_l2_vs_fp64_gpu"] = acc
     msl = rate(make_sim(256, "fp32", 2.0)[0], 4096)
     res["les_256_fp32_delta2"] = {"mlups": round(256 * 256 / msl / 1e3, 2)}
+    res["les_256_fp32_delta2_network"] = learned_closure_rate()
     res["ensemble_48"] = ensemble_measurement()
     torch.cuda.synchronize()
     return res
+
+
+def learned_closure_rate(k=2000):
+    """The 256^2 LES step with the learned correction attached (moments, features, three bf16
+    tensor-core convolution layers, correction, fused step per time step), with untrained
+    weights: the cost does not depend on their values."""
+    from paper_1705_09807_gb300 import lbmhd
+    from paper_1705_09807_gb300.inputs import splitmix64_uniform
+    n = 256
+    nparams = lbmhd.load_library().lbmhd_closure_num_params()
+    theta = ((2 * splitmix64_uniform(5, nparams) - 1) * 0.05).astype(np.float32)
+    cl = lbmhd.Closure(theta, np.full(12, 0.05, np.float32), np.full(4, 1e-6, np.float32))
+    sim, _ = make_sim(n, "fp32", 2.0)
+    cl.attach(sim.h)
+    sim.step(20)
+    l0 = sim.launches
+    ms = time_steps(sim, k) / k
+    launches = (sim.launches - l0) / k
+    lbmhd.lbmhd_detach_closure(sim.h)
+    sim.free()
+    cl.free()
+    # 2 x (12*32 + 32*32 + 32*4) x 9 flops per cell for the three convolutions
+    flops = 2 * 9 * (12 * 32 + 32 * 32 + 32 * 4) * n * n
+    return {"mlups": round(n * n / ms / 1e3, 2), "ms_per_step": round(ms, 5),
+            "launches_per_step": launches, "network_tflops_if_alone": round(flops / (ms * 1e-3) / 1e12, 2)}
 
 
 def ensemble_members(seed=4):
