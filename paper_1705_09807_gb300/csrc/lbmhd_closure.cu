@@ -194,8 +194,9 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
 
 // ---- bf16 tensor-core inference ----------------------------------------------------------------
 // Layer as an implicit GEMM: Y[cell][co] = b[co] + sum_k X[cell][k] W[co][k], k = ci*9 + tap,
-// K padded to a multiple of 16 with zeros.  A warp computes 16 consecutive cells of one row
-// (M = 16) for all CO (N tiles of 8) with mma.sync.m16n8k16 (bf16 x bf16 -> f32).
+// K padded to a multiple of 16 with zeros.  A block stages a 3-row bf16 patch of its 64-cell
+// row tile in shared memory; each warp computes 16 consecutive cells (M = 16) for all CO
+// (N tiles of 8) with mma.sync.m16n8k16 (bf16 x bf16 -> f32), reading A from the patch.
 // Fragment layouts of m16n8k16 (PTX ISA): with g = lane/4, q = lane%4,
 //   A regs (2 bf16 each): (g, 2q..), (g+8, 2q..), (g, 2q+8..), (g+8, 2q+8..)
 //   B regs: (k = 2q.., n = g), (k = 2q+8.., n = g)
@@ -213,40 +214,51 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+constexpr int kMmaTile = 64;  // cells of one row per block (4 warps x 16)
+
 template <int CI, int CO, bool TANH>
-__global__ void conv_fwd_mma_kernel(const float* __restrict__ in, const float* __restrict__ params,
-                                    int batch, int H, int W, float* __restrict__ out) {
+__global__ void __launch_bounds__(128) conv_fwd_mma_kernel(const float* __restrict__ in,
+                                                           const float* __restrict__ params, int batch,
+                                                           int H, int W, float* __restrict__ out) {
   constexpr int K = CI * 9;
   constexpr int KP = (K + 15) / 16 * 16;
   constexpr int NT = (CO + 7) / 8;        // n tiles of 8
   constexpr int NP = NT * 8;
-  // weights as bf16 [NP][KP] (co major, zero padded) and fp32 bias
+  constexpr int PW = kMmaTile + 2;        // staged columns: the tile plus one on each side
+  // weights as bf16 [NP][KP] (co major, zero padded), fp32 bias, the bf16 input patch
+  // [CI][3 rows][PW] of the tile, and for every k = ci*9 + tap its offset in the patch
   __shared__ __nv_bfloat16 sw[NP * KP];
   __shared__ float sb[NP];
+  __shared__ __nv_bfloat16 patch[CI * 3 * PW];
+  __shared__ int koff[KP];
   for (int i = threadIdx.x; i < NP * KP; i += blockDim.x) {
     const int co = i / KP, k = i % KP;
     sw[i] = __float2bfloat16_rn(co < CO && k < K ? params[co * K + k] : 0.f);
   }
   for (int i = threadIdx.x; i < NP; i += blockDim.x) sb[i] = i < CO ? params[CO * K + i] : 0.f;
-  __syncthreads();
+  for (int k = threadIdx.x; k < KP; k += blockDim.x) {
+    const int ci = k / 9, t = k % 9;
+    koff[k] = k < K ? ci * 3 * PW + (t / 3) * PW + (t % 3) : -1;
+  }
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-  const int warps = blockDim.x >> 5;
+  const int wm = (threadIdx.x >> 5) * 16;  // this warp's first cell in the tile
   const long plane = (long)H * W;
-  const long tiles = (long)batch * H * ((W + 15) / 16);  // 16-cell row segments
-  for (long tile = (long)blockIdx.x * warps + (threadIdx.x >> 5); tile < tiles; tile += (long)gridDim.x * warps) {
-    const int segs = (W + 15) / 16;
+  const int segs = (W + kMmaTile - 1) / kMmaTile;
+  const long tiles = (long)batch * H * segs;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int b = (int)(tile / ((long)H * segs));
     const int rem = (int)(tile % ((long)H * segs));
-    const int y = rem / segs, x0 = (rem % segs) * 16;
+    const int y = rem / segs, x0 = (rem % segs) * kMmaTile;
     const float* ib = in + (size_t)b * CI * plane;
-    // X[m][k] for this lane's rows m = g, g + 8 and column k
-    auto xval = [&](int m, int k) -> float {
-      if (k >= K) return 0.f;
-      const int ci = k / 9, t = k % 9;
-      const int xx = x0 + m;
-      if (xx >= W) return 0.f;
-      return ib[(size_t)ci * plane + wrapi(y + t / 3 - 1, H) * W + wrapi(xx + t % 3 - 1, W)];
-    };
+    __syncthreads();  // the previous tile's patch is no longer read (and the tables are ready)
+    for (int i = threadIdx.x; i < CI * 3 * PW; i += blockDim.x) {
+      const int ci = i / (3 * PW), r = (i / PW) % 3, cc = i % PW;
+      const int xx = x0 + cc - 1;
+      patch[i] = (xx <= W) ? __float2bfloat16_rn(ib[(size_t)ci * plane + wrapi(y + r - 1, H) * W + wrapi(xx, W)])
+                           : zero;
+    }
+    __syncthreads();
     float acc[NT][4];
 #pragma unroll
     for (int n = 0; n < NT; ++n) {
@@ -255,13 +267,21 @@ __global__ void conv_fwd_mma_kernel(const float* __restrict__ in, const float* _
       acc[n][2] = acc[n][0];
       acc[n][3] = acc[n][1];
     }
+    const int m0 = wm + g, m1 = wm + g + 8;
+    auto av = [&](int ko, int m) -> __nv_bfloat16 { return ko >= 0 ? patch[ko + m] : zero; };
+    auto pk = [](__nv_bfloat16 lo, __nv_bfloat16 hi) -> uint32_t {
+      __nv_bfloat162 v = __halves2bfloat162(lo, hi);
+      return *reinterpret_cast<uint32_t*>(&v);
+    };
 #pragma unroll 2
     for (int k0 = 0; k0 < KP; k0 += 16) {
+      const int o0 = koff[k0 + 2 * q], o1 = koff[k0 + 2 * q + 1];
+      const int o8 = koff[k0 + 2 * q + 8], o9 = koff[k0 + 2 * q + 9];
       uint32_t a[4];
-      a[0] = pack_bf16(xval(g, k0 + 2 * q), xval(g, k0 + 2 * q + 1));
-      a[1] = pack_bf16(xval(g + 8, k0 + 2 * q), xval(g + 8, k0 + 2 * q + 1));
-      a[2] = pack_bf16(xval(g, k0 + 2 * q + 8), xval(g, k0 + 2 * q + 9));
-      a[3] = pack_bf16(xval(g + 8, k0 + 2 * q + 8), xval(g + 8, k0 + 2 * q + 9));
+      a[0] = pk(av(o0, m0), av(o1, m0));
+      a[1] = pk(av(o0, m1), av(o1, m1));
+      a[2] = pk(av(o8, m0), av(o9, m0));
+      a[3] = pk(av(o8, m1), av(o9, m1));
 #pragma unroll
       for (int n = 0; n < NT; ++n) {
         const __nv_bfloat16* wb = sw + (n * 8 + g) * KP + k0;
@@ -276,7 +296,7 @@ __global__ void conv_fwd_mma_kernel(const float* __restrict__ in, const float* _
     for (int n = 0; n < NT; ++n) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const int m = g + (r >= 2 ? 8 : 0);
+        const int m = wm + g + (r >= 2 ? 8 : 0);
         const int co = n * 8 + 2 * q + (r & 1);
         const int xx = x0 + m;
         if (co < CO && xx < W) {
@@ -286,6 +306,12 @@ __global__ void conv_fwd_mma_kernel(const float* __restrict__ in, const float* _
       }
     }
   }
+}
+
+int mma_grid(int batch, int H, int W) {
+  long tiles = (long)batch * H * ((W + kMmaTile - 1) / kMmaTile);
+  if (tiles > 152L * 8) tiles = 152L * 8;
+  return tiles < 1 ? 1 : (int)tiles;
 }
 
 // ---- features and training targets ----------------------------------------------------------
@@ -416,7 +442,7 @@ cudaError_t closure_correction(const float* params, const float* in_scale, const
   const long mm = (long)m * m;
   features_kernel<<<grid_for(mm), kThreads, 0, s>>>(state, m, 1, in_scale, out_scale, 0.0, feat, nullptr,
                                                      nullptr, nullptr);
-  const int blocks = grid_for(mm / 16 + 1);
+  const int blocks = mma_grid(1, m, m);
   conv_fwd_mma_kernel<kC0, kC1, true><<<blocks, 128, 0, s>>>(feat, params, 1, m, m, a1);
   conv_fwd_mma_kernel<kC1, kC2, true><<<blocks, 128, 0, s>>>(a1, params + kP1, 1, m, m, a2);
   conv_fwd_mma_kernel<kC2, kC3, false><<<blocks, 128, 0, s>>>(a2, params + kP1 + kP2, 1, m, m, corr);
@@ -630,7 +656,7 @@ int lbmhd_closure_forward(lbmhd_closure_t* c, const float* x, int batch, int h, 
   const float* p3 = c->params + kP1 + kP2;
   cudaStream_t s = c->stream;
   if (tensor_cores) {
-    const int blocks = grid_for((long)batch * h * ((w + 15) / 16) / 4 + 1);
+    const int blocks = mma_grid(batch, h, w);
     conv_fwd_mma_kernel<kC0, kC1, true><<<blocks, 128, 0, s>>>(x, p1, batch, h, w, c->a1);
     conv_fwd_mma_kernel<kC1, kC2, true><<<blocks, 128, 0, s>>>(c->a1, p2, batch, h, w, c->a2);
     conv_fwd_mma_kernel<kC2, kC3, false><<<blocks, 128, 0, s>>>(c->a2, p3, batch, h, w, out);
