@@ -45,8 +45,8 @@ NU = ETA = 2e-3   # see the module docstring
 # 2048^2 workload, from an ncu capture; keyed by the SHA-256 of the kernel source it was taken
 # on, so a changed kernel reports null until it is measured again.
 MEASURED_TRAFFIC = {
-    # profiles/fused_step_fp32_2048.md: (470.37 + 408.00 + 470.47 + 405.75) MB / 2 launches
-    ("2fd94697584f2316", 2048, "fp32", 0.0): 877.30e6,
+    # profiles/fused_step_fp32_2048.md: (470.38 + 408.12 + 470.39 + 405.38) MB / 2 launches
+    ("7f01c118ec88054f", 2048, "fp32", 0.0): 877.14e6,
 }
 
 

@@ -225,13 +225,21 @@ void lbmhd_closure_free(lbmhd_closure_t* c);
  * outlive the attachment and must not be trained while attached. */
 int lbmhd_set_closure(lbmhd_t* h, lbmhd_closure_t* c);
 
+/* Failure-detection test hook.  With enable = 1, the first block of every following step
+ * leaves out one of its staged-row copies, so its time-bounded wait (2 s) runs out: the block
+ * records a timeout, drains its other copies and stops, no GPU fault occurs, and the next
+ * synchronising call returns LBMHD_ERR_TIMEOUT.  enable = 0 restores normal steps;
+ * lbmhd_set_state clears the timeout status.  For tests of the error path only. */
+int lbmhd_test_skip_row_copy(lbmhd_t* h, int enable);
+
 /* Size in bytes of a checkpoint of this handle's state. */
 size_t lbmhd_state_bytes(const lbmhd_t* h);
 
 /* Copy the raw population state to / from a host buffer of exactly lbmhd_state_bytes(h)
  * bytes (checkpoint / resume; restoring and stepping reproduces the run bitwise).  The
  * format is the handle's storage (precision, row pitch); restore only into a handle made
- * with the same nx, ny and precision.  Both synchronise. */
+ * with the same nx, ny and precision.  Both synchronise; set_state also clears a pipeline-timeout
+ * status (LBMHD_ERR_TIMEOUT), since the restored state is valid. */
 int lbmhd_get_state(lbmhd_t* h, void* host_buf, size_t bytes);
 int lbmhd_set_state(lbmhd_t* h, const void* host_buf, size_t bytes);
 

@@ -525,6 +525,18 @@ int lbmhd_energy_spectrum(lbmhd_t* h, int nbins, double* e_kin, double* e_mag) {
   return check_step_status(h);
 }
 
+int lbmhd_test_skip_row_copy(lbmhd_t* h, int enable) {
+  if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (h->in_ensemble) return fail(h, LBMHD_ERR_INVALID, "not for ensemble members");
+  h->geom.skip_copy = enable ? 1 : 0;
+  for (int i = 0; i < 2; ++i)  // captured graphs hold the old geometry
+    if (h->graph[i]) {
+      cudaGraphExecDestroy(h->graph[i]);
+      h->graph[i] = nullptr;
+    }
+  return LBMHD_OK;
+}
+
 int lbmhd_set_correction_device(lbmhd_t* h, const float* corr) {
   if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
   if (corr && h->precision == LBMHD_FP16)
@@ -568,6 +580,8 @@ int lbmhd_set_state(lbmhd_t* h, const void* host_buf, size_t bytes) {
   if (!host_buf || bytes != h->state_bytes)
     return fail(h, LBMHD_ERR_INVALID, "state buffer must be %zu bytes", h->state_bytes);
   LB_CUDA(h, cudaMemcpyAsync(h->pops[h->cur], host_buf, bytes, cudaMemcpyHostToDevice, h->stream));
+  // a restored state is valid again: clear a pipeline-timeout status
+  LB_CUDA(h, cudaMemsetAsync(h->err_flag, 0, sizeof(unsigned), h->stream));
   LB_CUDA(h, cudaStreamSynchronize(h->stream));
   h->steps = 0;
   return LBMHD_OK;

@@ -201,11 +201,6 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
 //   A regs (2 bf16 each): (g, 2q..), (g+8, 2q..), (g, 2q+8..), (g+8, 2q+8..)
 //   B regs: (k = 2q.., n = g), (k = 2q+8.., n = g)
 //   C/D:    (g, 2q), (g, 2q+1), (g+8, 2q), (g+8, 2q+1)
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&h);
-}
-
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "

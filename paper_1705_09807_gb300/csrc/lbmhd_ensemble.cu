@@ -105,6 +105,7 @@ int build_work(lbmhd_ensemble_t* e, int rows_per_tile, int persistent) {
   std::vector<StepGeom> geoms(e->n);
   for (int i : order) {
     StepGeom g = e->members[i]->geom;
+    g.skip_copy = 0;
     g.band = rows_per_tile > 0 ? std::min(rows_per_tile, g.ny)
                                : step_band_rows(g.nx, g.ny, e->precision, e->num_sms);
     if (g.band < 1) g.band = 1;

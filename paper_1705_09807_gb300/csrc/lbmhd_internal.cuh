@@ -84,6 +84,8 @@ struct StepGeom {
   int nx, ny, pitch;  // grid and row pitch (elements)
   size_t plane;       // elements per plane = pitch * ny
   int band;           // rows per block
+  int skip_copy;      // test hook: 1 = block (0, 0) never issues its third row copy, so its
+                      // bounded wait runs out and the step reports a timeout (no fault)
 };
 
 // Fused step launchers (lbmhd_step.cu).  `src` is a 3-D tensor map {pitch, ny, 27} of the

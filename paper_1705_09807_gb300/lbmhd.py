@@ -112,6 +112,7 @@ def load_library(path: str | None = None):
             "lbmhd_ensemble_last_error": (ctypes.c_char_p, [_H]),
             "lbmhd_ensemble_free": (None, [_H]),
             "lbmhd_set_correction_device": (ctypes.c_int, [_H, ctypes.c_void_p]),
+            "lbmhd_test_skip_row_copy": (ctypes.c_int, [_H, ctypes.c_int]),
             "lbmhd_set_closure": (ctypes.c_int, [_H, ctypes.c_void_p]),
             "lbmhd_closure_num_params": (ctypes.c_int, []),
             "lbmhd_closure_create": (ctypes.c_int, [ctypes.POINTER(_H), _F, _F, _F]),
@@ -300,6 +301,10 @@ def lbmhd_get_state(h) -> np.ndarray:
 def lbmhd_set_state(h, buf) -> None:
     buf = np.ascontiguousarray(buf, dtype=np.uint8)
     _check(load_library().lbmhd_set_state(h, buf.ctypes.data, buf.nbytes), h)
+
+
+def lbmhd_test_skip_row_copy(h, enable: bool) -> None:
+    _check(load_library().lbmhd_test_skip_row_copy(h, 1 if enable else 0), h)
 
 
 def lbmhd_get_stream(h) -> int:

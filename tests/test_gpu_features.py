@@ -168,3 +168,31 @@ def test_argument_errors_on_a_live_handle():
         assert sim.launches == launches
         sim.step(65)
         assert sim.launches == launches + 65 and sim.steps == 65
+
+
+@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32])
+def test_pipeline_wait_timeout_reported_and_context_usable(precision):
+    """Failure detection without a fault: one block leaves out one staged-row copy, so its
+    time-bounded mbarrier wait runs out; the step reports LBMHD_ERR_TIMEOUT to the host, the
+    context stays usable, and a restored checkpoint continues the run exactly."""
+    import time
+    fields = kh_jet(96, seed=6)
+    with lbmhd.Lbmhd(_params(96, precision), *fields) as ref:
+        ref.step(5)
+        want = ref.populations()
+    with lbmhd.Lbmhd(_params(96, precision), *fields) as sim:
+        sim.step(4)
+        ck = sim.get_state()
+        lbmhd.lbmhd_test_skip_row_copy(sim.h, True)
+        t0 = time.perf_counter()
+        sim.step(1)
+        with pytest.raises(lbmhd.LbmhdError) as e:
+            sim.moments()
+        assert e.value.code == lbmhd.LBMHD_ERR_TIMEOUT
+        assert "timed out" in lbmhd.lbmhd_last_error(sim.h)
+        assert time.perf_counter() - t0 > 1.5  # the wait limit, not an early exit
+        lbmhd.lbmhd_test_skip_row_copy(sim.h, False)
+        sim.set_state(ck)
+        sim.step(1)
+        sim.moments()  # status clear again
+        assert np.array_equal(sim.populations(), want)
