@@ -251,14 +251,10 @@ int one_step_corrected(lbmhd_t* h) {
     double* f = h->fields;
     LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, f, f + mm, f + 2 * mm, f + 3 * mm,
                               f + 4 * mm, h->stream));
-    const float* sc = closure_device_scales(h->closure);
     float* feat = h->cl_buf;
-    float* a1 = feat + 12 * mm;
-    float* a2 = a1 + 32 * mm;
-    float* c = a2 + 32 * mm;
-    LB_CUDA(h, closure_correction(closure_device_params(h->closure), sc, sc + 12, f, m, feat, a1, a2, c,
-                                  h->stream));
-    h->launches += 6;
+    float* c = feat + 12 * mm;
+    LB_CUDA(h, closure_correction(h->closure, f, m, feat, c, h->err_flag, h->stream));
+    h->launches += 3;
     corr = c;
   }
   const int nxt = h->cur ^ 1;
@@ -555,7 +551,7 @@ int lbmhd_set_closure(lbmhd_t* h, lbmhd_closure_t* c) {
     if (h->corr_static) return fail(h, LBMHD_ERR_INVALID, "detach the static correction first");
     if (!h->cl_buf) {
       const size_t mm = (size_t)h->p.nx * h->p.ny;
-      LB_CUDA(h, cudaMalloc(&h->cl_buf, (12 + 32 + 32 + 4) * mm * sizeof(float)));
+      LB_CUDA(h, cudaMalloc(&h->cl_buf, (12 + 4) * mm * sizeof(float)));
     }
     // the closure's parameters must be in place before this handle's stream reads them
     LB_CUDA(h, cudaStreamSynchronize(closure_stream(c)));

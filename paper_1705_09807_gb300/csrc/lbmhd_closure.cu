@@ -2,8 +2,9 @@
 // channels, tanh after the first two layers) that predicts the residual between the exact
 // filtered subgrid terms and the analytic Delta^2/12 closure of Sec. 2.1 / Sec. 3.  This file
 // holds its training kernels (binary32 forward, back-propagation, Adam), its inference kernel
-// (bf16 operands on the tensor cores through mma.sync m16n8k16, binary32 accumulation), and the
-// kernels that build features and training targets from filtered fine-grid fields.
+// (all three layers fused in one kernel on the 5th-generation tensor cores: bf16 operands in
+// shared memory, tcgen05.mma, fp32 accumulators in tensor memory), and the kernels that build
+// features and training targets from filtered fine-grid fields.
 //
 // Conventions (shared with the C ABI): activations are [batch][channel][H][W] binary32 planes on
 // a periodic H x W grid; parameters are one flat binary32 vector holding, per layer,
@@ -21,6 +22,7 @@
 #include "lbmhd.h"
 #include "lbmhd_handle.h"
 #include "lbmhd_internal.cuh"
+#include "lbmhd_ptx.cuh"
 
 namespace lbmhd_gpu {
 namespace {
@@ -32,6 +34,7 @@ constexpr int kP3 = kC3 * kC2 * 9 + kC3;          // 1156
 constexpr int kNumParams = kP1 + kP2 + kP3;       // 13892
 constexpr int kThreads = 256;
 constexpr int kWeightCellsPerBlock = 1024;        // cells per block in the weight-gradient pass
+constexpr uint64_t kNetWaitNs = 2000000000ull;    // bound of every tensor-core completion wait
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
@@ -192,121 +195,284 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
   }
 }
 
-// ---- bf16 tensor-core inference ----------------------------------------------------------------
-// Layer as an implicit GEMM: Y[cell][co] = b[co] + sum_k X[cell][k] W[co][k], k = ci*9 + tap,
-// K padded to a multiple of 16 with zeros.  A block stages a 3-row bf16 patch of its 64-cell
-// row tile in shared memory; each warp computes 16 consecutive cells (M = 16) for all CO
-// (N tiles of 8) with mma.sync.m16n8k16 (bf16 x bf16 -> f32), reading A from the patch.
-// Fragment layouts of m16n8k16 (PTX ISA): with g = lane/4, q = lane%4,
-//   A regs (2 bf16 each): (g, 2q..), (g+8, 2q..), (g, 2q+8..), (g+8, 2q+8..)
-//   B regs: (k = 2q.., n = g), (k = 2q+8.., n = g)
-//   C/D:    (g, 2q), (g, 2q+1), (g+8, 2q), (g+8, 2q+1)
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+// ---- bf16 tensor-core inference: the whole network in one kernel (tcgen05 + TMEM) --------------
+// A CTA computes a kTT x kTT tile of the output from a kPS x kPS patch (3 cells of halo, one per
+// layer) held in shared memory as bf16.  Each 3x3 layer is, per 128-cell M tile, nine shifted
+// implicit GEMMs per 16-channel K chunk, D[cell][co] += A[cell + dy kPS + dx][k] W_tap[co][k],
+// issued by one thread as tcgen05.mma (M = 128, N = 32, or 16 for the 4-channel last layer,
+// K = 16) with the fp32 accumulators in tensor memory; the epilogue reads them back with
+// tcgen05.ld (one cell per thread), adds the bias, applies tanh and stores the next layer's bf16
+// input.  The patch is indexed linearly (cell = row kPS + col), so the shifts wrap across rows:
+// the results wrapped that way lie in the halo, which shrinks by one cell per layer, and are
+// never used by the kept outputs.
+//
+// Shared-memory operand layouts (no swizzle, K-major core matrices of 8 rows x 16 bytes):
+//   activations: [8-channel chunk][cell] x 16 B; consecutive cells 16 B apart, so an 8-cell group
+//     is one core matrix (stride byte offset 128 B), the next 8 channels one chunk further
+//     (leading byte offset kChunkBytes), and a shift by s cells is a start address 16 s B later.
+//   weights: per (tap, 16-channel K chunk) an N x 16 block with (n, k) at (n%8) 16 + (n/8) 256 +
+//     (k/8) 128 + (k%8) 2 bytes (leading byte offset 128, stride byte offset 256).
+constexpr int kTT = 16;                       // output tile side
+constexpr int kPS = kTT + 6;                  // patch side: 22
+constexpr int kPatch = kPS * kPS;             // 484 cells
+constexpr int kMT = 4;                        // M tiles of layers 1 and 2: cells 0 .. 511
+constexpr int kL3First = 64, kL3Tiles = 3;    // layer 3: cells 64 .. 447 (rows / cols 3 .. 18)
+constexpr int kPadCells = 24;                 // zero cells before and after each chunk (>= kPS + 1)
+constexpr int kChunkCells = kPadCells + kMT * 128 + kPadCells;  // 560
+constexpr int kChunkBytes = kChunkCells * 16;                   // 8960
+constexpr int kW1Bytes = 9 * 1 * 32 * 32;     // taps x K chunks x (N rows x 32 B)
+constexpr int kW2Bytes = 9 * 2 * 32 * 32;
+constexpr int kW3Bytes = 9 * 2 * 16 * 32;
+constexpr int kWBytes = kW1Bytes + kW2Bytes + kW3Bytes;         // 36864
+constexpr int kBiasFloats = 32 + 32 + 16;
+constexpr int kPackedBytes = kWBytes + kBiasFloats * 4;         // weights then biases
+// shared memory map (bytes from the 128-byte aligned base)
+constexpr int kSmW = 0;
+constexpr int kSmXA = kSmW + kWBytes;                 // features, then layer-2 output (4 chunks)
+constexpr int kSmX1 = kSmXA + 4 * kChunkBytes;        // layer-1 output (4 chunks)
+constexpr int kSmBias = kSmX1 + 4 * kChunkBytes;      // 80 biases + 4 output scales
+constexpr int kSmBar = kSmBias + (kBiasFloats + 4) * 4;
+constexpr int kSmSlot = kSmBar + 8;
+constexpr int kNetSmemBytes = kSmSlot + 8 + 128;      // + alignment slack
+constexpr uint32_t kTmemCols = 128;                   // 4 M tiles x 32 fp32 columns
+constexpr int kNetThreads = 128;
+static_assert(kSmBar % 8 == 0, "mbarrier alignment");
+static_assert(kPadCells >= kPS + 1, "shifted reads stay inside a chunk");
+static_assert(kL3First + 128 * kL3Tiles > (kPS - 4) * kPS + kPS - 4, "layer-3 tiles cover the output");
+
+// Weights and biases of the three layers in the shared-memory layout above (bf16 weights,
+// fp32 biases, zero padding for ci >= CI and co >= CO).
+__global__ void pack_net_kernel(const float* __restrict__ params, unsigned char* __restrict__ packed) {
+  __nv_bfloat16* w = reinterpret_cast<__nv_bfloat16*>(packed);
+  float* bias = reinterpret_cast<float*>(packed + kWBytes);
+  const int nw = kWBytes / 2;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw + kBiasFloats; i += gridDim.x * blockDim.x) {
+    if (i >= nw) {
+      const int j = i - nw;
+      const int layer = j < 32 ? 0 : (j < 64 ? 1 : 2);
+      const int co = j - 32 * layer;
+      const int CI = layer == 0 ? kC0 : kC1, CO = layer == 2 ? kC3 : kC1;
+      const int base = layer == 0 ? 0 : (layer == 1 ? kP1 : kP1 + kP2);
+      bias[j] = co < CO ? params[base + CO * CI * 9 + co] : 0.f;
+      continue;
+    }
+    int byte = 2 * i, N, nkc, CI, CO, base;
+    if (byte < kW1Bytes) {
+      N = 32, nkc = 1, CI = kC0, CO = kC1, base = 0;
+    } else if (byte < kW1Bytes + kW2Bytes) {
+      N = 32, nkc = 2, CI = kC1, CO = kC2, base = kP1, byte -= kW1Bytes;
+    } else {
+      N = 16, nkc = 2, CI = kC2, CO = kC3, base = kP1 + kP2, byte -= kW1Bytes + kW2Bytes;
+    }
+    const int blk = byte / (N * 32), in = byte % (N * 32);
+    const int tap = blk / nkc, kc = blk % nkc;
+    const int n = (in / 256) * 8 + (in % 128) / 16;
+    const int k = ((in % 256) / 128) * 8 + (in % 16) / 2;
+    const int ci = 16 * kc + k;
+    w[i] = __float2bfloat16_rn(n < CO && ci < CI ? params[base + n * CI * 9 + ci * 9 + tap] : 0.f);
+  }
 }
 
-constexpr int kMmaTile = 64;  // cells of one row per block (4 warps x 16)
+__device__ __forceinline__ int wrap_mod(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
 
-template <int CI, int CO, bool TANH>
-__global__ void __launch_bounds__(128) conv_fwd_mma_kernel(const float* __restrict__ in,
-                                                           const float* __restrict__ params, int batch,
-                                                           int H, int W, float* __restrict__ out) {
-  constexpr int K = CI * 9;
-  constexpr int KP = (K + 15) / 16 * 16;
-  constexpr int NT = (CO + 7) / 8;        // n tiles of 8
-  constexpr int NP = NT * 8;
-  constexpr int PW = kMmaTile + 2;        // staged columns: the tile plus one on each side
-  // weights as bf16 [NP][KP] (co major, zero padded), fp32 bias, the bf16 input patch
-  // [CI][3 rows][PW] of the tile, and for every k = ci*9 + tap its offset in the patch
-  __shared__ __nv_bfloat16 sw[NP * KP];
-  __shared__ float sb[NP];
-  __shared__ __nv_bfloat16 patch[CI * 3 * PW];
-  __shared__ int koff[KP];
-  for (int i = threadIdx.x; i < NP * KP; i += blockDim.x) {
-    const int co = i / KP, k = i % KP;
-    sw[i] = __float2bfloat16_rn(co < CO && k < K ? params[co * K + k] : 0.f);
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Issue one layer: for each M tile, 9 taps x nkc K chunks into TMEM columns mt * n; then commit.
+__device__ __forceinline__ void issue_layer(uint32_t sbase, int act_off, int w_off, int n, int nkc, int first_cell,
+                                            int ntiles, uint32_t tmem, uint64_t* bar) {
+  const uint32_t idesc = idesc_bf16_f32(128, n);
+  for (int mt = 0; mt < ntiles; ++mt) {
+    for (int tap = 0; tap < 9; ++tap) {
+      const int shift = (tap / 3 - 1) * kPS + (tap % 3 - 1);
+      const int cell = kPadCells + first_cell + mt * 128 + shift;
+      for (int kc = 0; kc < nkc; ++kc) {
+        const uint64_t a = smem_desc(sbase + act_off + 2 * kc * kChunkBytes + cell * 16, kChunkBytes, 128);
+        const uint64_t b = smem_desc(sbase + w_off + (tap * nkc + kc) * (n * 32), 128, 256);
+        tc_mma_bf16(tmem + mt * n, a, b, idesc, (tap | kc) != 0);
+      }
+    }
   }
-  for (int i = threadIdx.x; i < NP; i += blockDim.x) sb[i] = i < CO ? params[CO * K + i] : 0.f;
-  for (int k = threadIdx.x; k < KP; k += blockDim.x) {
-    const int ci = k / 9, t = k % 9;
-    koff[k] = k < K ? ci * 3 * PW + (t / 3) * PW + (t % 3) : -1;
+  tc_commit(bar);
+}
+
+// Epilogue of a hidden layer: tanh(D + b) of this thread's cell in each M tile -> bf16 chunks.
+__device__ __forceinline__ void hidden_epilogue(uint32_t tmem, const float* __restrict__ bias,
+                                                unsigned char* __restrict__ dst) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (int mt = 0; mt < kMT; ++mt) {
+    uint32_t r[32];
+    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + mt * 32, r);
+    tmem_ld_wait();
+    const int cell = mt * 128 + 32 * warp + lane;
+    uint32_t pk[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      pk[j] = bf16x2(tanh_approx(__uint_as_float(r[2 * j]) + bias[2 * j]),
+                     tanh_approx(__uint_as_float(r[2 * j + 1]) + bias[2 * j + 1]));
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      *reinterpret_cast<uint4*>(dst + c * kChunkBytes + (kPadCells + cell) * 16) =
+          make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
   }
-  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-  const int wm = (threadIdx.x >> 5) * 16;  // this warp's first cell in the tile
+}
+
+// All CTA threads wait for the layer's MMAs; false (uniformly) if the bounded wait ran out.
+__device__ __forceinline__ bool wait_layer(uint64_t* bar, uint32_t& phase) {
+  const bool ok = mbar_wait_bounded(bar, phase, kNetWaitNs);
+  phase ^= 1u;
+  tc_fence_after();
+  return !__syncthreads_or(!ok);
+}
+
+// Persistent over tiles (batch x tiles_y x tiles_x).  in: features [batch][12][H][W] fp32;
+// out: [batch][4][H][W] fp32 = (network output) x oscale[co] (oscale NULL: 1).
+__global__ void __launch_bounds__(kNetThreads, 2)
+    net_tc_kernel(const float* __restrict__ in, const unsigned char* __restrict__ packed,
+                  const float* __restrict__ oscale, int batch, int H, int W, float* __restrict__ out,
+                  unsigned* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char net_smem_raw[];
+  unsigned char* sm = net_smem_raw + ((128u - (smem_u32(net_smem_raw) & 127u)) & 127u);
+  const uint32_t sbase = smem_u32(sm);
+  float* bias = reinterpret_cast<float*>(sm + kSmBias);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kSmBar);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + kSmSlot);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  for (int i = tid; i < kWBytes / 16; i += kNetThreads)
+    reinterpret_cast<uint4*>(sm + kSmW)[i] = reinterpret_cast<const uint4*>(packed)[i];
+  for (int i = tid; i < kBiasFloats + 4; i += kNetThreads)
+    bias[i] = i < kBiasFloats ? reinterpret_cast<const float*>(packed + kWBytes)[i]
+                              : (oscale ? oscale[i - kBiasFloats] : 1.f);
+  // zero pad cells of the 8 activation chunks (shifted reads reach kPS + 1 cells beyond 0 .. 511)
+  for (int i = tid; i < 8 * 2 * kPadCells; i += kNetThreads) {
+    const int ch = i / (2 * kPadCells), j = i % (2 * kPadCells);
+    const int cell = j < kPadCells ? j : kMT * 128 + j;
+    *reinterpret_cast<uint4*>(sm + kSmXA + ch * kChunkBytes + cell * 16) = make_uint4(0, 0, 0, 0);
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(slot, kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+
   const long plane = (long)H * W;
-  const int segs = (W + kMmaTile - 1) / kMmaTile;
-  const long tiles = (long)batch * H * segs;
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-  for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int b = (int)(tile / ((long)H * segs));
-    const int rem = (int)(tile % ((long)H * segs));
-    const int y = rem / segs, x0 = (rem % segs) * kMmaTile;
-    const float* ib = in + (size_t)b * CI * plane;
-    __syncthreads();  // the previous tile's patch is no longer read (and the tables are ready)
-    for (int i = threadIdx.x; i < CI * 3 * PW; i += blockDim.x) {
-      const int ci = i / (3 * PW), r = (i / PW) % 3, cc = i % PW;
-      const int xx = x0 + cc - 1;
-      patch[i] = (xx <= W) ? __float2bfloat16_rn(ib[(size_t)ci * plane + wrapi(y + r - 1, H) * W + wrapi(xx, W)])
-                           : zero;
+  const int tiles_x = (W + kTT - 1) / kTT, tiles_y = (H + kTT - 1) / kTT;
+  const long ntiles = (long)batch * tiles_x * tiles_y;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int b = (int)(tile / ((long)tiles_x * tiles_y));
+    const int rem = (int)(tile % ((long)tiles_x * tiles_y));
+    const int ty0 = (rem / tiles_x) * kTT, tx0 = (rem % tiles_x) * kTT;
+    const float* ib = in + (size_t)b * kC0 * plane;
+    // features of the patch (rows ty0 - 3 .., cols tx0 - 3 .., periodic) -> chunks 0, 1 of XA
+    for (int cell = tid; cell < kMT * 128; cell += kNetThreads) {
+      uint32_t w8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (cell < kPatch) {
+        const int gy = wrap_mod(ty0 - 3 + cell / kPS, H), gx = wrap_mod(tx0 - 3 + cell % kPS, W);
+        const float* p = ib + (size_t)gy * W + gx;
+#pragma unroll
+        for (int j = 0; j < kC0 / 2; ++j) w8[j] = bf16x2(p[(2 * j) * plane], p[(2 * j + 1) * plane]);
+      }
+      *reinterpret_cast<uint4*>(sm + kSmXA + (kPadCells + cell) * 16) = make_uint4(w8[0], w8[1], w8[2], w8[3]);
+      *reinterpret_cast<uint4*>(sm + kSmXA + kChunkBytes + (kPadCells + cell) * 16) =
+          make_uint4(w8[4], w8[5], w8[6], w8[7]);
     }
+    fence_proxy_async_smem();
+    tc_fence_before();
     __syncthreads();
-    float acc[NT][4];
+    tc_fence_after();
+    // layer 1: 12 (padded to 16) -> 32
+    if (tid == 0) issue_layer(sbase, kSmXA, kSmW, 32, 1, 0, kMT, tmem, bar);
+    if (!(ok = wait_layer(bar, phase))) break;
+    hidden_epilogue(tmem, bias, sm + kSmX1);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // layer 2: 32 -> 32
+    if (tid == 0) issue_layer(sbase, kSmX1, kSmW + kW1Bytes, 32, 2, 0, kMT, tmem, bar);
+    if (!(ok = wait_layer(bar, phase))) break;
+    hidden_epilogue(tmem, bias + 32, sm + kSmXA);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // layer 3: 32 -> 4 (N = 16), only the M tiles that hold the kept outputs
+    if (tid == 0) issue_layer(sbase, kSmXA, kSmW + kW1Bytes + kW2Bytes, 16, 2, kL3First, kL3Tiles, tmem, bar);
+    if (!(ok = wait_layer(bar, phase))) break;
+#pragma unroll 1
+    for (int mt = 0; mt < kL3Tiles; ++mt) {
+      uint32_t r[4];
+      tmem_ld4(tmem + ((uint32_t)(32 * warp) << 16) + mt * 16, r);
+      tmem_ld_wait();
+      const int cell = kL3First + mt * 128 + 32 * warp + lane;
+      const int pr = cell / kPS, pc = cell % kPS;
+      const int gy = ty0 + pr - 3, gx = tx0 + pc - 3;
+      if (pr >= 3 && pr < 3 + kTT && pc >= 3 && pc < 3 + kTT && gy < H && gx < W) {
+        float* ob = out + (size_t)b * kC3 * plane + (size_t)gy * W + gx;
 #pragma unroll
-    for (int n = 0; n < NT; ++n) {
-      acc[n][0] = sb[n * 8 + 2 * q];
-      acc[n][1] = sb[n * 8 + 2 * q + 1];
-      acc[n][2] = acc[n][0];
-      acc[n][3] = acc[n][1];
-    }
-    const int m0 = wm + g, m1 = wm + g + 8;
-    auto av = [&](int ko, int m) -> __nv_bfloat16 { return ko >= 0 ? patch[ko + m] : zero; };
-    auto pk = [](__nv_bfloat16 lo, __nv_bfloat16 hi) -> uint32_t {
-      __nv_bfloat162 v = __halves2bfloat162(lo, hi);
-      return *reinterpret_cast<uint32_t*>(&v);
-    };
-#pragma unroll 2
-    for (int k0 = 0; k0 < KP; k0 += 16) {
-      const int o0 = koff[k0 + 2 * q], o1 = koff[k0 + 2 * q + 1];
-      const int o8 = koff[k0 + 2 * q + 8], o9 = koff[k0 + 2 * q + 9];
-      uint32_t a[4];
-      a[0] = pk(av(o0, m0), av(o1, m0));
-      a[1] = pk(av(o0, m1), av(o1, m1));
-      a[2] = pk(av(o8, m0), av(o9, m0));
-      a[3] = pk(av(o8, m1), av(o9, m1));
-#pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        const __nv_bfloat16* wb = sw + (n * 8 + g) * KP + k0;
-        uint32_t bfr[2];
-        bfr[0] = *reinterpret_cast<const uint32_t*>(wb + 2 * q);
-        bfr[1] = *reinterpret_cast<const uint32_t*>(wb + 2 * q + 8);
-        mma_bf16_16816(acc[n], a, bfr);
+        for (int co = 0; co < kC3; ++co)
+          ob[co * plane] = (__uint_as_float(r[co]) + bias[64 + co]) * bias[kBiasFloats + co];
       }
     }
-    float* ob = out + (size_t)b * CO * plane;
-#pragma unroll
-    for (int n = 0; n < NT; ++n) {
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int m = wm + g + (r >= 2 ? 8 : 0);
-        const int co = n * 8 + 2 * q + (r & 1);
-        const int xx = x0 + m;
-        if (co < CO && xx < W) {
-          const float v = acc[n][r];
-          ob[(size_t)co * plane + (size_t)y * W + xx] = TANH ? tanhf(v) : v;
-        }
-      }
-    }
+    // TMEM reads and shared-memory operands of this tile are finished before the next tile
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
   }
+  if (!ok) {
+    if (tid == 0) {
+      atomicOr(err, 1u);
+      mbar_wait_bounded(bar, phase ^ 1u, kNetWaitNs);  // let the outstanding MMAs drain
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-int mma_grid(int batch, int H, int W) {
-  long tiles = (long)batch * H * ((W + kMmaTile - 1) / kMmaTile);
-  if (tiles > 152L * 8) tiles = 152L * 8;
-  return tiles < 1 ? 1 : (int)tiles;
+int net_grid(int batch, int H, int W, int num_sms) {
+  const long tiles = (long)batch * ((H + kTT - 1) / kTT) * ((W + kTT - 1) / kTT);
+  const long cap = 2L * num_sms;
+  return (int)(tiles < cap ? (tiles < 1 ? 1 : tiles) : cap);
+}
+
+cudaError_t launch_net(const float* in, const unsigned char* packed, const float* oscale, int batch, int H,
+                       int W, float* out, unsigned* err, cudaStream_t s) {
+  int dev = 0, sms = 152;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static bool attr_set[64] = {};
+  if (dev < 64 && !attr_set[dev]) {
+    e = cudaFuncSetAttribute(net_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kNetSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  net_tc_kernel<<<net_grid(batch, H, W, sms), kNetThreads, kNetSmemBytes, s>>>(in, packed, oscale, batch, H, W,
+                                                                               out, err);
+  return cudaGetLastError();
 }
 
 // ---- features and training targets ----------------------------------------------------------
@@ -414,11 +580,6 @@ __global__ void features_kernel(const double* __restrict__ st, int m, int veloci
 }
 
 // correction (4 planes, physical units) = network output x out_scale; in place
-__global__ void scale_output_kernel(float* __restrict__ out, long mm, const float* __restrict__ out_scale) {
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < 4 * mm; c += (long)gridDim.x * blockDim.x)
-    out[c] *= out_scale[c / mm];
-}
-
 int grid_for(long n) {
   long b = (n + kThreads - 1) / kThreads;
   if (b > 152L * 16) b = 152L * 16;
@@ -430,19 +591,16 @@ int grid_for(long n) {
 int closure_num_params() { return kNumParams; }
 
 // Inference on a coarse state: moments (rho, Jx, Jy, Bx, By planes, binary64) -> correction
-// planes [4][m][m] in physical units, via features and the bf16 tensor-core network.
-cudaError_t closure_correction(const float* params, const float* in_scale, const float* out_scale,
-                               const double* state, int m, float* feat, float* a1, float* a2,
-                               float* corr, cudaStream_t s) {
+// planes [4][m][m] in physical units, via features and the fused tensor-core network.
+cudaError_t closure_correction(const lbmhd_closure_t* c, const double* state, int m, float* feat, float* corr,
+                               unsigned* err, cudaStream_t s) {
   const long mm = (long)m * m;
-  features_kernel<<<grid_for(mm), kThreads, 0, s>>>(state, m, 1, in_scale, out_scale, 0.0, feat, nullptr,
-                                                     nullptr, nullptr);
-  const int blocks = mma_grid(1, m, m);
-  conv_fwd_mma_kernel<kC0, kC1, true><<<blocks, 128, 0, s>>>(feat, params, 1, m, m, a1);
-  conv_fwd_mma_kernel<kC1, kC2, true><<<blocks, 128, 0, s>>>(a1, params + kP1, 1, m, m, a2);
-  conv_fwd_mma_kernel<kC2, kC3, false><<<blocks, 128, 0, s>>>(a2, params + kP1 + kP2, 1, m, m, corr);
-  scale_output_kernel<<<grid_for(4 * mm), kThreads, 0, s>>>(corr, mm, out_scale);
-  return cudaGetLastError();
+  const float* sc = closure_device_scales(c);
+  features_kernel<<<grid_for(mm), kThreads, 0, s>>>(state, m, 1, sc, sc + 12, 0.0, feat, nullptr, nullptr,
+                                                     nullptr);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_net(feat, closure_device_packed(c), sc + 12, 1, m, m, corr, err, s);
 }
 
 }  // namespace lbmhd_gpu
@@ -456,6 +614,8 @@ struct lbmhd_closure {
   float* adam_m = nullptr;
   float* adam_v = nullptr;
   float* scales = nullptr;  // device: in_scale[12], out_scale[4]
+  unsigned char* packed = nullptr;  // device: bf16 weights + fp32 biases for the tensor-core kernel
+  unsigned* tc_err = nullptr;       // device: tensor-core wait timeout flag
   float host_scales[16];
   int adam_t = 0;
   // training scratch (grown on demand)
@@ -546,6 +706,13 @@ int forward_backward(lbmhd_closure_t* c, const float* x, const float* t, int bat
   return LBMHD_OK;
 }
 
+// Refresh the tensor-core copy of the parameters (after any change of c->params).
+int repack(lbmhd_closure_t* c) {
+  pack_net_kernel<<<(kWBytes / 2 + kBiasFloats + 255) / 256, 256, 0, c->stream>>>(c->params, c->packed);
+  CL_CUDA(c, cudaGetLastError());
+  return LBMHD_OK;
+}
+
 void destroy_closure(lbmhd_closure_t* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -554,6 +721,8 @@ void destroy_closure(lbmhd_closure_t* c) {
   for (float* b : bufs)
     if (b) cudaFree(b);
   if (c->lpart) cudaFree(c->lpart);
+  if (c->packed) cudaFree(c->packed);
+  if (c->tc_err) cudaFree(c->tc_err);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -583,10 +752,18 @@ int lbmhd_closure_create(lbmhd_closure_t** out, const float* params, const float
   if (e == cudaSuccess) e = cudaMalloc(&c->adam_m, pb);
   if (e == cudaSuccess) e = cudaMalloc(&c->adam_v, pb);
   if (e == cudaSuccess) e = cudaMalloc(&c->scales, 16 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&c->packed, kPackedBytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->tc_err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(c->tc_err, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemcpy(c->params, params, pb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->adam_m, 0, pb);
   if (e == cudaSuccess) e = cudaMemset(c->adam_v, 0, pb);
   if (e == cudaSuccess) e = cudaMemcpy(c->scales, c->host_scales, 16 * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    pack_net_kernel<<<(kWBytes / 2 + kBiasFloats + 255) / 256, 256, 0, c->stream>>>(c->params, c->packed);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     int rc = cfail(nullptr, e == cudaErrorMemoryAllocation ? LBMHD_ERR_OOM : LBMHD_ERR_CUDA,
                    cudaGetErrorString(e));
@@ -611,6 +788,9 @@ int lbmhd_closure_set_params(lbmhd_closure_t* c, const float* params) {
   c->adam_t = 0;
   CL_CUDA(c, cudaMemset(c->adam_m, 0, kNumParams * sizeof(float)));
   CL_CUDA(c, cudaMemset(c->adam_v, 0, kNumParams * sizeof(float)));
+  int rc = repack(c);
+  if (rc) return rc;
+  CL_CUDA(c, cudaStreamSynchronize(c->stream));
   return LBMHD_OK;
 }
 
@@ -636,7 +816,7 @@ int lbmhd_closure_train_step(lbmhd_closure_t* c, const float* x, const float* t,
   adam_kernel<<<grid_for(kNumParams), kThreads, 0, c->stream>>>(c->params, c->grad, c->adam_m, c->adam_v,
                                                                 kNumParams, lr, b1, b2, 1e-8f, c1, c2);
   CL_CUDA(c, cudaGetLastError());
-  return LBMHD_OK;
+  return repack(c);
 }
 
 int lbmhd_closure_forward(lbmhd_closure_t* c, const float* x, int batch, int h, int w, float* out,
@@ -651,10 +831,7 @@ int lbmhd_closure_forward(lbmhd_closure_t* c, const float* x, int batch, int h, 
   const float* p3 = c->params + kP1 + kP2;
   cudaStream_t s = c->stream;
   if (tensor_cores) {
-    const int blocks = mma_grid(batch, h, w);
-    conv_fwd_mma_kernel<kC0, kC1, true><<<blocks, 128, 0, s>>>(x, p1, batch, h, w, c->a1);
-    conv_fwd_mma_kernel<kC1, kC2, true><<<blocks, 128, 0, s>>>(c->a1, p2, batch, h, w, c->a2);
-    conv_fwd_mma_kernel<kC2, kC3, false><<<blocks, 128, 0, s>>>(c->a2, p3, batch, h, w, out);
+    CL_CUDA(c, launch_net(x, c->packed, nullptr, batch, h, w, out, c->tc_err, s));
   } else {
     const int g = grid_for((long)cells);
     conv_fwd_kernel<kC0, kC1, true><<<g, kThreads, 0, s>>>(x, p1, batch, h, w, c->a1);
@@ -663,6 +840,14 @@ int lbmhd_closure_forward(lbmhd_closure_t* c, const float* x, int batch, int h, 
   }
   CL_CUDA(c, cudaGetLastError());
   CL_CUDA(c, cudaStreamSynchronize(s));
+  if (tensor_cores) {
+    unsigned v = 0;
+    CL_CUDA(c, cudaMemcpy(&v, c->tc_err, sizeof v, cudaMemcpyDeviceToHost));
+    if (v) {
+      CL_CUDA(c, cudaMemset(c->tc_err, 0, sizeof v));
+      return cfail(c, LBMHD_ERR_TIMEOUT, "a tensor-core completion wait timed out");
+    }
+  }
   return LBMHD_OK;
 }
 
@@ -705,5 +890,6 @@ namespace lbmhd_gpu {
 // Device pointers of a closure's parameters and scales (for handles that attach it).
 const float* closure_device_params(const lbmhd_closure_t* c) { return c->params; }
 const float* closure_device_scales(const lbmhd_closure_t* c) { return c->scales; }
+const unsigned char* closure_device_packed(const lbmhd_closure_t* c) { return c->packed; }
 cudaStream_t closure_stream(const lbmhd_closure_t* c) { return c->stream; }
 }  // namespace lbmhd_gpu

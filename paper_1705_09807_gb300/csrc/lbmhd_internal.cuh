@@ -145,15 +145,16 @@ cudaError_t launch_energy_spectrum(const double* ux, const double* uy, const dou
                                    void* work, cudaStream_t s);
 
 // Learned closure (lbmhd_closure.cu): correction planes [4][m][m] for a square coarse state
-// given as binary64 planes (rho, ux, uy, bx, by), via features and the bf16 tensor-core network.
-// feat: 12 m^2 floats; a1, a2: 32 m^2 floats each; corr: 4 m^2 floats.
+// given as binary64 planes (rho, ux, uy, bx, by), via features and the fused tensor-core network
+// (2 launches).  feat: 12 m^2 floats; corr: 4 m^2 floats; *err is set if a tensor-core wait
+// times out.
 int closure_num_params();
-cudaError_t closure_correction(const float* params, const float* in_scale, const float* out_scale,
-                               const double* state, int m, float* feat, float* a1, float* a2,
-                               float* corr, cudaStream_t s);
+cudaError_t closure_correction(const lbmhd_closure_t* c, const double* state, int m, float* feat, float* corr,
+                               unsigned* err, cudaStream_t s);
 
 const float* closure_device_params(const lbmhd_closure_t* c);
 const float* closure_device_scales(const lbmhd_closure_t* c);
+const unsigned char* closure_device_packed(const lbmhd_closure_t* c);
 cudaStream_t closure_stream(const lbmhd_closure_t* c);
 
 // Store a message for lbmhd_last_error(NULL) on the calling thread (lbmhd_api.cu).
