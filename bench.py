@@ -365,9 +365,10 @@ def side_measurements(n, a):
 
 
 def learned_closure_rate(k=2000):
-    """The 256^2 LES step with the learned correction attached (moments, features, three bf16
-    tensor-core convolution layers, correction, fused step per time step), with untrained
-    weights: the cost does not depend on their values."""
+    """The 256^2 LES step with the learned correction attached (per time step: one fused
+    network launch -- pull, u and B, features, three bf16 tcgen05 layers, output scale -- and
+    the corrected fused step), with untrained weights: the cost does not depend on their
+    values."""
     from paper_1705_09807_gb300 import lbmhd
     from paper_1705_09807_gb300.inputs import splitmix64_uniform
     n = 256

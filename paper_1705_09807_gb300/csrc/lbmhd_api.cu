@@ -246,16 +246,10 @@ cudaError_t launch_one(lbmhd_t* h, int from, int to, const float* corr = nullptr
 int one_step_corrected(lbmhd_t* h) {
   const float* corr = h->corr_static;
   if (h->closure) {
-    const int m = h->p.nx;
-    const size_t mm = (size_t)m * m;
-    double* f = h->fields;
-    LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, f, f + mm, f + 2 * mm, f + 3 * mm,
-                              f + 4 * mm, h->stream));
-    float* feat = h->cl_buf;
-    float* c = feat + 12 * mm;
-    LB_CUDA(h, closure_correction(h->closure, f, m, feat, c, h->err_flag, h->stream));
-    h->launches += 3;
-    corr = c;
+    LB_CUDA(h, closure_correction(h->closure, h->precision, h->pops[h->cur], h->geom, h->cl_buf, h->err_flag,
+                                  h->stream));
+    h->launches += 1;
+    corr = h->cl_buf;
   }
   const int nxt = h->cur ^ 1;
   cudaError_t e = launch_one(h, h->cur, nxt, corr);
@@ -551,7 +545,7 @@ int lbmhd_set_closure(lbmhd_t* h, lbmhd_closure_t* c) {
     if (h->corr_static) return fail(h, LBMHD_ERR_INVALID, "detach the static correction first");
     if (!h->cl_buf) {
       const size_t mm = (size_t)h->p.nx * h->p.ny;
-      LB_CUDA(h, cudaMalloc(&h->cl_buf, (12 + 4) * mm * sizeof(float)));
+      LB_CUDA(h, cudaMalloc(&h->cl_buf, 4 * mm * sizeof(float)));
     }
     // the closure's parameters must be in place before this handle's stream reads them
     LB_CUDA(h, cudaStreamSynchronize(closure_stream(c)));

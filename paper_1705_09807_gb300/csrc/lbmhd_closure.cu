@@ -230,13 +230,15 @@ constexpr int kPackedBytes = kWBytes + kBiasFloats * 4;         // weights then 
 constexpr int kSmW = 0;
 constexpr int kSmXA = kSmW + kWBytes;                 // features, then layer-2 output (4 chunks)
 constexpr int kSmX1 = kSmXA + 4 * kChunkBytes;        // layer-1 output (4 chunks)
-constexpr int kSmBias = kSmX1 + 4 * kChunkBytes;      // 80 biases + 4 output scales
-constexpr int kSmBar = kSmBias + (kBiasFloats + 4) * 4;
-constexpr int kSmSlot = kSmBar + 8;
+constexpr int kSmBias = kSmX1 + 4 * kChunkBytes;      // 80 biases, 4 output scales, 12 1/in_scale
+constexpr int kSmBar = kSmBias + (kBiasFloats + 4 + 12) * 4;  // layer barrier, weight-copy barrier
+constexpr int kSmSlot = kSmBar + 16;
 constexpr int kNetSmemBytes = kSmSlot + 8 + 128;      // + alignment slack
+constexpr int kMS = kPS + 2;                          // moment grid side for the features: 24
 constexpr uint32_t kTmemCols = 128;                   // 4 M tiles x 32 fp32 columns
 constexpr int kNetThreads = 128;
 static_assert(kSmBar % 8 == 0, "mbarrier alignment");
+static_assert(5 * kMS * kMS * 4 <= 4 * kChunkBytes, "moments fit in the layer-1 output buffer");
 static_assert(kPadCells >= kPS + 1, "shifted reads stay inside a chunk");
 static_assert(kL3First + 128 * kL3Tiles > (kPS - 4) * kPS + kPS - 4, "layer-3 tiles cover the output");
 
@@ -329,42 +331,144 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem, const float* __re
   }
 }
 
-// All CTA threads wait for the layer's MMAs; false (uniformly) if the bounded wait ran out.
-__device__ __forceinline__ bool wait_layer(uint64_t* bar, uint32_t& phase) {
-  const bool ok = mbar_wait_bounded(bar, phase, kNetWaitNs);
+// All CTA threads wait for the layer's MMAs; false (uniformly) if a bounded wait ran out here or
+// `mine` is false in some thread.
+__device__ __forceinline__ bool wait_layer(uint64_t* bar, uint32_t& phase, bool mine) {
+  const bool ok = mbar_wait_bounded(bar, phase, kNetWaitNs) && mine;
   phase ^= 1u;
   tc_fence_after();
   return !__syncthreads_or(!ok);
 }
 
-// Persistent over tiles (batch x tiles_y x tiles_x).  in: features [batch][12][H][W] fp32;
-// out: [batch][4][H][W] fp32 = (network output) x oscale[co] (oscale NULL: 1).
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// The 16 input channels (12 features, 4 zeros) of patch cell `cell` -> XA chunks 0, 1 (bf16).
+__device__ __forceinline__ void put_features(unsigned char* sm, int cell, const float (&f)[12]) {
+  uint32_t w8[8];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) w8[j] = bf16x2(f[2 * j], f[2 * j + 1]);
+  w8[6] = w8[7] = 0u;
+  *reinterpret_cast<uint4*>(sm + kSmXA + (kPadCells + cell) * 16) = make_uint4(w8[0], w8[1], w8[2], w8[3]);
+  *reinterpret_cast<uint4*>(sm + kSmXA + kChunkBytes + (kPadCells + cell) * 16) =
+      make_uint4(w8[4], w8[5], w8[6], w8[7]);
+}
+
+// Patch input from feature planes [batch][12][H][W] (scaled already).
+__device__ __forceinline__ void load_features(unsigned char* sm, const float* __restrict__ ib, long plane, int H,
+                                              int W, int ty0, int tx0) {
+  for (int cell = threadIdx.x; cell < kMT * 128; cell += kNetThreads) {
+    float f[12];
+    if (cell < kPatch) {
+      const int gy = wrap_mod(ty0 - 3 + cell / kPS, H), gx = wrap_mod(tx0 - 3 + cell % kPS, W);
+      const float* p = ib + (size_t)gy * W + gx;
+#pragma unroll
+      for (int k = 0; k < kC0; ++k) f[k] = p[k * plane];
+    } else {
+#pragma unroll
+      for (int k = 0; k < kC0; ++k) f[k] = 0.f;
+    }
+    put_features(sm, cell, f);
+  }
+}
+
+// Patch input from the populations of a square grid: pull the 27 populations of each cell of
+// the 24 x 24 moment grid (origin ty0 - 4, tx0 - 4), form u = J / rho and B in binary32 (layer-1
+// output buffer as scratch), then the features of the 22 x 22 patch: u_x, u_y, B_x, B_y and
+// their central differences (d_x, d_y of each in turn), each times 1 / in_scale.
+template <typename S>
+__device__ __forceinline__ void load_from_pops(unsigned char* sm, const S* __restrict__ pops, const StepGeom& g,
+                                               int ty0, int tx0, const float* __restrict__ inv_s) {
+  float* mom = reinterpret_cast<float*>(sm + kSmX1);
+  constexpr int MM = kMS * kMS;
+#pragma unroll 2
+  for (int cell = threadIdx.x; cell < MM; cell += kNetThreads) {
+    const int y = wrap_mod(ty0 - 4 + cell / kMS, g.ny), x = wrap_mod(tx0 - 4 + cell % kMS, g.nx);
+    float v[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      const int i = q % 9;
+      const int sx = wrapi(x - vel_x(i), g.nx), sy = wrapi(y - vel_y(i), g.ny);
+      v[q] = load_as<float>(pops[(size_t)plane_of(q) * g.plane + (size_t)sy * g.pitch + kXOff + sx]);
+    }
+    const float rho1 = (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) + v[8];
+    const float jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
+    const float jy = (v[2] - v[4]) + (v[5] - v[8]) + (v[6] - v[7]);
+    float bx = 0.f, by = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      bx += v[9 + i];
+      by += v[18 + i];
+    }
+    const float r = 1.f + rho1;
+    mom[cell] = jx / r;
+    mom[MM + cell] = jy / r;
+    mom[2 * MM + cell] = bx;
+    mom[3 * MM + cell] = by;
+  }
+  __syncthreads();
+  for (int cell = threadIdx.x; cell < kMT * 128; cell += kNetThreads) {
+    float f[12];
+    if (cell < kPatch) {
+      const int o = (cell / kPS + 1) * kMS + cell % kPS + 1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float* a = mom + k * MM;
+        f[k] = a[o] * inv_s[k];
+        f[4 + 2 * k] = 0.5f * (a[o + 1] - a[o - 1]) * inv_s[4 + 2 * k];
+        f[5 + 2 * k] = 0.5f * (a[o + kMS] - a[o - kMS]) * inv_s[5 + 2 * k];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kC0; ++k) f[k] = 0.f;
+    }
+    put_features(sm, cell, f);
+  }
+}
+
+// Persistent over tiles (batch x tiles_y x tiles_x).  SRC 0: src = features [batch][12][H][W]
+// fp32; SRC 1 / 2: src = binary32 / binary64 populations of the square grid g (batch 1, H = ny,
+// W = nx), features formed here with in_scale.  out: [batch][4][H][W] fp32 = (network output)
+// x oscale[co] (oscale NULL: 1).
+template <int SRC>
 __global__ void __launch_bounds__(kNetThreads, 2)
-    net_tc_kernel(const float* __restrict__ in, const unsigned char* __restrict__ packed,
-                  const float* __restrict__ oscale, int batch, int H, int W, float* __restrict__ out,
-                  unsigned* __restrict__ err) {
+    net_tc_kernel(const void* __restrict__ src, StepGeom g, const float* __restrict__ in_scale,
+                  const unsigned char* __restrict__ packed, const float* __restrict__ oscale, int batch, int H,
+                  int W, float* __restrict__ out, unsigned* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char net_smem_raw[];
   unsigned char* sm = net_smem_raw + ((128u - (smem_u32(net_smem_raw) & 127u)) & 127u);
   const uint32_t sbase = smem_u32(sm);
   float* bias = reinterpret_cast<float*>(sm + kSmBias);
+  float* inv_s = bias + kBiasFloats + 4;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kSmBar);
+  uint64_t* wbar = bar + 1;
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + kSmSlot);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  for (int i = tid; i < kWBytes / 16; i += kNetThreads)
-    reinterpret_cast<uint4*>(sm + kSmW)[i] = reinterpret_cast<const uint4*>(packed)[i];
-  for (int i = tid; i < kBiasFloats + 4; i += kNetThreads)
-    bias[i] = i < kBiasFloats ? reinterpret_cast<const float*>(packed + kWBytes)[i]
-                              : (oscale ? oscale[i - kBiasFloats] : 1.f);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(wbar, 1);
+    fence_barrier_init();
+    // the weights (bf16, already in the operand layout) arrive by one bulk copy
+    mbar_arrive_expect_tx(wbar, kWBytes);
+    bulk_copy_g2s(sm + kSmW, packed, kWBytes, wbar);
+  }
+  for (int i = tid; i < kBiasFloats + 4 + 12; i += kNetThreads) {
+    float v;
+    if (i < kBiasFloats) v = reinterpret_cast<const float*>(packed + kWBytes)[i];
+    else if (i < kBiasFloats + 4) v = oscale ? oscale[i - kBiasFloats] : 1.f;
+    else v = SRC ? 1.f / in_scale[i - kBiasFloats - 4] : 1.f;
+    bias[i] = v;
+  }
   // zero pad cells of the 8 activation chunks (shifted reads reach kPS + 1 cells beyond 0 .. 511)
   for (int i = tid; i < 8 * 2 * kPadCells; i += kNetThreads) {
     const int ch = i / (2 * kPadCells), j = i % (2 * kPadCells);
     const int cell = j < kPadCells ? j : kMT * 128 + j;
     *reinterpret_cast<uint4*>(sm + kSmXA + ch * kChunkBytes + cell * 16) = make_uint4(0, 0, 0, 0);
-  }
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    fence_barrier_init();
   }
   if (warp == 0) {
     tmem_alloc(slot, kTmemCols);
@@ -379,32 +483,29 @@ __global__ void __launch_bounds__(kNetThreads, 2)
   const int tiles_x = (W + kTT - 1) / kTT, tiles_y = (H + kTT - 1) / kTT;
   const long ntiles = (long)batch * tiles_x * tiles_y;
   uint32_t phase = 0;
-  bool ok = true;
+  bool ok = true, weights_ready = false;
   for (long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const int b = (int)(tile / ((long)tiles_x * tiles_y));
     const int rem = (int)(tile % ((long)tiles_x * tiles_y));
     const int ty0 = (rem / tiles_x) * kTT, tx0 = (rem % tiles_x) * kTT;
-    const float* ib = in + (size_t)b * kC0 * plane;
-    // features of the patch (rows ty0 - 3 .., cols tx0 - 3 .., periodic) -> chunks 0, 1 of XA
-    for (int cell = tid; cell < kMT * 128; cell += kNetThreads) {
-      uint32_t w8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (cell < kPatch) {
-        const int gy = wrap_mod(ty0 - 3 + cell / kPS, H), gx = wrap_mod(tx0 - 3 + cell % kPS, W);
-        const float* p = ib + (size_t)gy * W + gx;
-#pragma unroll
-        for (int j = 0; j < kC0 / 2; ++j) w8[j] = bf16x2(p[(2 * j) * plane], p[(2 * j + 1) * plane]);
-      }
-      *reinterpret_cast<uint4*>(sm + kSmXA + (kPadCells + cell) * 16) = make_uint4(w8[0], w8[1], w8[2], w8[3]);
-      *reinterpret_cast<uint4*>(sm + kSmXA + kChunkBytes + (kPadCells + cell) * 16) =
-          make_uint4(w8[4], w8[5], w8[6], w8[7]);
-    }
+    if (SRC == 0)
+      load_features(sm, static_cast<const float*>(src) + (size_t)b * kC0 * plane, plane, H, W, ty0, tx0);
+    else if (SRC == 1)
+      load_from_pops<float>(sm, static_cast<const float*>(src), g, ty0, tx0, inv_s);
+    else
+      load_from_pops<double>(sm, static_cast<const double*>(src), g, ty0, tx0, inv_s);
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     // layer 1: 12 (padded to 16) -> 32
-    if (tid == 0) issue_layer(sbase, kSmXA, kSmW, 32, 1, 0, kMT, tmem, bar);
-    if (!(ok = wait_layer(bar, phase))) break;
+    bool mine = true;
+    if (tid == 0) {
+      if (!weights_ready) mine = weights_ready = mbar_wait_bounded(wbar, 0, kNetWaitNs);
+      if (mine) issue_layer(sbase, kSmXA, kSmW, 32, 1, 0, kMT, tmem, bar);
+      else tc_commit(bar);
+    }
+    if (!(ok = wait_layer(bar, phase, mine))) break;
     hidden_epilogue(tmem, bias, sm + kSmX1);
     fence_proxy_async_smem();
     tc_fence_before();
@@ -412,7 +513,7 @@ __global__ void __launch_bounds__(kNetThreads, 2)
     tc_fence_after();
     // layer 2: 32 -> 32
     if (tid == 0) issue_layer(sbase, kSmX1, kSmW + kW1Bytes, 32, 2, 0, kMT, tmem, bar);
-    if (!(ok = wait_layer(bar, phase))) break;
+    if (!(ok = wait_layer(bar, phase, true))) break;
     hidden_epilogue(tmem, bias + 32, sm + kSmXA);
     fence_proxy_async_smem();
     tc_fence_before();
@@ -420,7 +521,7 @@ __global__ void __launch_bounds__(kNetThreads, 2)
     tc_fence_after();
     // layer 3: 32 -> 4 (N = 16), only the M tiles that hold the kept outputs
     if (tid == 0) issue_layer(sbase, kSmXA, kSmW + kW1Bytes + kW2Bytes, 16, 2, kL3First, kL3Tiles, tmem, bar);
-    if (!(ok = wait_layer(bar, phase))) break;
+    if (!(ok = wait_layer(bar, phase, true))) break;
 #pragma unroll 1
     for (int mt = 0; mt < kL3Tiles; ++mt) {
       uint32_t r[4];
@@ -441,14 +542,15 @@ __global__ void __launch_bounds__(kNetThreads, 2)
     __syncthreads();
     tc_fence_after();
   }
-  if (!ok) {
-    if (tid == 0) {
+  if (tid == 0) {
+    if (!ok) {
       atomicOr(err, 1u);
-      mbar_wait_bounded(bar, phase ^ 1u, kNetWaitNs);  // let the outstanding MMAs drain
+      mbar_wait_bounded(bar, phase ^ 1u, kNetWaitNs);  // let outstanding MMAs drain
     }
-    tc_fence_before();
-    __syncthreads();
+    if (!weights_ready) mbar_wait_bounded(wbar, 0, kNetWaitNs);  // the weight copy has landed
   }
+  tc_fence_before();
+  __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
@@ -458,21 +560,28 @@ int net_grid(int batch, int H, int W, int num_sms) {
   return (int)(tiles < cap ? (tiles < 1 ? 1 : tiles) : cap);
 }
 
-cudaError_t launch_net(const float* in, const unsigned char* packed, const float* oscale, int batch, int H,
-                       int W, float* out, unsigned* err, cudaStream_t s) {
+template <int SRC>
+cudaError_t launch_net_impl(const void* src, const StepGeom& g, const float* in_scale, const unsigned char* packed,
+                            const float* oscale, int batch, int H, int W, float* out, unsigned* err,
+                            cudaStream_t s) {
   int dev = 0, sms = 152;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   static bool attr_set[64] = {};
   if (dev < 64 && !attr_set[dev]) {
-    e = cudaFuncSetAttribute(net_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kNetSmemBytes);
+    e = cudaFuncSetAttribute(net_tc_kernel<SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNetSmemBytes);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  net_tc_kernel<<<net_grid(batch, H, W, sms), kNetThreads, kNetSmemBytes, s>>>(in, packed, oscale, batch, H, W,
-                                                                               out, err);
+  net_tc_kernel<SRC><<<net_grid(batch, H, W, sms), kNetThreads, kNetSmemBytes, s>>>(src, g, in_scale, packed, oscale,
+                                                                                    batch, H, W, out, err);
   return cudaGetLastError();
+}
+
+cudaError_t launch_net(const float* in, const unsigned char* packed, const float* oscale, int batch, int H,
+                       int W, float* out, unsigned* err, cudaStream_t s) {
+  return launch_net_impl<0>(in, StepGeom{}, nullptr, packed, oscale, batch, H, W, out, err, s);
 }
 
 // ---- features and training targets ----------------------------------------------------------
@@ -590,17 +699,15 @@ int grid_for(long n) {
 
 int closure_num_params() { return kNumParams; }
 
-// Inference on a coarse state: moments (rho, Jx, Jy, Bx, By planes, binary64) -> correction
-// planes [4][m][m] in physical units, via features and the fused tensor-core network.
-cudaError_t closure_correction(const lbmhd_closure_t* c, const double* state, int m, float* feat, float* corr,
-                               unsigned* err, cudaStream_t s) {
-  const long mm = (long)m * m;
+// Correction planes [4][m][m] (physical units) for the current populations of a square
+// binary64 / binary32 grid: one launch of the fused network kernel (pull, u and B, features,
+// three tensor-core layers, output scale).
+cudaError_t closure_correction(const lbmhd_closure_t* c, int precision, const void* pops, const StepGeom& g,
+                               float* corr, unsigned* err, cudaStream_t s) {
   const float* sc = closure_device_scales(c);
-  features_kernel<<<grid_for(mm), kThreads, 0, s>>>(state, m, 1, sc, sc + 12, 0.0, feat, nullptr, nullptr,
-                                                     nullptr);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return launch_net(feat, closure_device_packed(c), sc + 12, 1, m, m, corr, err, s);
+  const unsigned char* pk = closure_device_packed(c);
+  if (precision == 0) return launch_net_impl<2>(pops, g, sc, pk, sc + 12, 1, g.ny, g.nx, corr, err, s);
+  return launch_net_impl<1>(pops, g, sc, pk, sc + 12, 1, g.ny, g.nx, corr, err, s);
 }
 
 }  // namespace lbmhd_gpu

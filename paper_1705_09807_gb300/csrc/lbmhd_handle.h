@@ -32,7 +32,7 @@ struct lbmhd {
   void* spec_work = nullptr;       // spectrum work buffer and outputs (allocated on first use)
   const float* corr_static = nullptr;    // caller's correction planes [4][ny][nx] (not owned)
   struct lbmhd_closure* closure = nullptr;  // attached learned closure (not owned)
-  float* cl_buf = nullptr;         // closure scratch: features 12, correction 4 planes
+  float* cl_buf = nullptr;         // closure correction planes [4][ny][nx]
   uint64_t launches = 0;
   int64_t steps = 0;
   std::string err;

@@ -144,13 +144,12 @@ cudaError_t launch_energy_spectrum(const double* ux, const double* uy, const dou
                                    const double* by, int n, int nbins, double* ek, double* em,
                                    void* work, cudaStream_t s);
 
-// Learned closure (lbmhd_closure.cu): correction planes [4][m][m] for a square coarse state
-// given as binary64 planes (rho, ux, uy, bx, by), via features and the fused tensor-core network
-// (2 launches).  feat: 12 m^2 floats; corr: 4 m^2 floats; *err is set if a tensor-core wait
-// times out.
+// Learned closure (lbmhd_closure.cu): correction planes corr [4][ny][nx] (physical units) for
+// the current populations of a square binary64 (precision 0) or binary32 (1) grid, in one launch
+// of the fused tensor-core network kernel; *err is set if one of its waits times out.
 int closure_num_params();
-cudaError_t closure_correction(const lbmhd_closure_t* c, const double* state, int m, float* feat, float* corr,
-                               unsigned* err, cudaStream_t s);
+cudaError_t closure_correction(const lbmhd_closure_t* c, int precision, const void* pops, const StepGeom& g,
+                               float* corr, unsigned* err, cudaStream_t s);
 
 const float* closure_device_params(const lbmhd_closure_t* c);
 const float* closure_device_scales(const lbmhd_closure_t* c);

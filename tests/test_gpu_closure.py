@@ -115,16 +115,24 @@ def test_static_correction_matches_oracle(precision, tol):
     assert np.max(np.abs(np.concatenate([fp, gp.reshape(18, ny, nx)]) - ref)) > 1e-6
 
 
-def test_closure_in_the_loop_equals_its_static_correction():
+@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32])
+def test_closure_in_the_loop_matches_its_static_correction(precision):
+    """The attached closure forms u, B and the features from the populations in binary32 inside
+    its one fused network launch; the same correction by hand goes through the binary64 moments,
+    the features entry point and the forward pass.  They differ only by the rounding of the
+    features (and so, rarely, of their bf16 copies), so the corrected steps agree to a small
+    fraction of the correction's own effect on the populations."""
     import torch
     n = 64
     f = kh_jet(n, seed=5)
     s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
-    p = lbmhd.make_params(n, n, s, sm, 2.0, lbmhd.LBMHD_FP32)
-    with lbmhd.Closure(_params(), IN_SCALE, OUT_SCALE) as cl, \
-            lbmhd.Lbmhd(p, *f) as a, lbmhd.Lbmhd(p, *f) as b:
+    p = lbmhd.make_params(n, n, s, sm, 2.0, precision)
+    with lbmhd.Closure(_params(), IN_SCALE, OUT_SCALE) as cl, lbmhd.Lbmhd(p, *f) as a, \
+            lbmhd.Lbmhd(p, *f) as b, lbmhd.Lbmhd(p, *f) as plain:
         cl.attach(a.h)
+        launches = a.launches
         a.step(1)
+        assert a.launches == launches + 2  # network + corrected step
         # the same correction by hand: moments -> features -> tensor-core network -> scale
         st = [torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(5)]
         b.moments_device(st)
@@ -136,7 +144,12 @@ def test_closure_in_the_loop_equals_its_static_correction():
         corr = (out[0] * torch.tensor(OUT_SCALE, device="cuda")[:, None, None]).contiguous()
         lbmhd.lbmhd_set_correction_device(b.h, corr)
         b.step(1)
-        assert np.array_equal(a.populations(), b.populations())
+        plain.step(1)
+        pa, pb, pp = a.populations(), b.populations(), plain.populations()
+        effect = pb - pp
+        assert np.max(np.abs(effect)) > 0
+        assert np.max(np.abs(pa - pb)) < 5e-2 * np.max(np.abs(effect))
+        assert np.sqrt(np.mean((pa - pb) ** 2)) < 1e-2 * np.sqrt(np.mean(effect ** 2))
         lbmhd.lbmhd_detach_closure(a.h)
         a.step(2)  # back to the analytic closure alone
 
