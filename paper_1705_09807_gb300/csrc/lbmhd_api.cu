@@ -241,23 +241,29 @@ cudaError_t launch_one(lbmhd_t* h, int from, int to, const float* corr = nullptr
   }
 }
 
-// One step with the attached correction: the caller's static planes, or the learned closure's
-// output for the current state (moments -> features -> network -> correction -> step).
-int one_step_corrected(lbmhd_t* h) {
-  const float* corr = h->corr_static;
+// The launches of one step from copy `from` into copy `to`: with an attached learned closure,
+// its network (correction of the current state) and the corrected step; with static correction
+// planes, the corrected step; else the plain step.  *nlaunch receives the number of launches.
+cudaError_t launch_step_seq(lbmhd_t* h, int from, int to, int* nlaunch) {
+  *nlaunch = 1;
   if (h->closure) {
-    LB_CUDA(h, closure_correction(h->closure, h->precision, h->pops[h->cur], h->geom, h->cl_buf, h->err_flag,
-                                  h->stream));
-    h->launches += 1;
-    corr = h->cl_buf;
+    cudaError_t e = closure_correction(h->closure, h->precision, h->pops[from], h->geom, h->cl_buf, h->err_flag,
+                                       h->stream);
+    if (e != cudaSuccess) return e;
+    *nlaunch = 2;
+    return launch_one(h, from, to, h->cl_buf);
   }
-  const int nxt = h->cur ^ 1;
-  cudaError_t e = launch_one(h, h->cur, nxt, corr);
-  if (e != cudaSuccess) return cuda_fail(h, e, "fused step launch (corrected)");
-  h->cur = nxt;
-  h->launches += 1;
-  h->steps += 1;
-  return LBMHD_OK;
+  return launch_one(h, from, to, h->corr_static);
+}
+
+// Captured graphs hold kernel arguments (geometry, correction planes, closure): drop them when
+// any of those changes.
+void drop_graphs(lbmhd_t* h) {
+  for (int i = 0; i < 2; ++i)
+    if (h->graph[i]) {
+      cudaGraphExecDestroy(h->graph[i]);
+      h->graph[i] = nullptr;
+    }
 }
 
 int build_graph(lbmhd_t* h, int parity) {
@@ -265,11 +271,13 @@ int build_graph(lbmhd_t* h, int parity) {
   LB_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   int cur = parity;
   cudaError_t le = cudaSuccess;
+  int per_step = 1;
   for (int n = 0; n < kGraphSteps && le == cudaSuccess; ++n) {
     const int nxt = cur ^ 1;
-    le = launch_one(h, cur, nxt);
+    le = launch_step_seq(h, cur, nxt, &per_step);
     cur = nxt;
   }
+  h->graph_launches = kGraphSteps * per_step;
   cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
   if (le != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -287,11 +295,11 @@ int build_graph(lbmhd_t* h, int parity) {
 
 int one_step(lbmhd_t* h) {
   const int nxt = h->cur ^ 1;
-  cudaError_t e;
-  e = launch_one(h, h->cur, nxt);
+  int nl = 1;
+  cudaError_t e = launch_step_seq(h, h->cur, nxt, &nl);
   if (e != cudaSuccess) return cuda_fail(h, e, "fused step launch");
   h->cur = nxt;
-  h->launches += 1;
+  h->launches += nl;
   h->steps += 1;
   return LBMHD_OK;
 }
@@ -398,14 +406,7 @@ int lbmhd_step(lbmhd_t* h, int nsteps) {
     return fail(h, LBMHD_ERR_INVALID, "this handle is an ensemble member: step the ensemble");
   if (nsteps < 0) return fail(h, LBMHD_ERR_INVALID, "nsteps = %d < 0", nsteps);
   int n = nsteps;
-  if (h->corr_static || h->closure) {
-    for (; n > 0; --n) {
-      int rc = one_step_corrected(h);
-      if (rc) return rc;
-    }
-    return LBMHD_OK;
-  }
-  // whole graphs of kGraphSteps launches when the handle owns its stream
+  // whole graphs of kGraphSteps steps when the handle owns its stream
   if (h->own_stream && n >= kGraphSteps) {
     if (!h->graph[h->cur]) {
       int rc = build_graph(h, h->cur);
@@ -413,7 +414,7 @@ int lbmhd_step(lbmhd_t* h, int nsteps) {
     }
     while (n >= kGraphSteps) {
       LB_CUDA(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
-      h->launches += kGraphSteps;
+      h->launches += h->graph_launches;
       h->steps += kGraphSteps;
       n -= kGraphSteps;  // kGraphSteps is even: h->cur is unchanged
     }
@@ -519,11 +520,7 @@ int lbmhd_test_skip_row_copy(lbmhd_t* h, int enable) {
   if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
   if (h->in_ensemble) return fail(h, LBMHD_ERR_INVALID, "not for ensemble members");
   h->geom.skip_copy = enable ? 1 : 0;
-  for (int i = 0; i < 2; ++i)  // captured graphs hold the old geometry
-    if (h->graph[i]) {
-      cudaGraphExecDestroy(h->graph[i]);
-      h->graph[i] = nullptr;
-    }
+  drop_graphs(h);
   return LBMHD_OK;
 }
 
@@ -533,6 +530,7 @@ int lbmhd_set_correction_device(lbmhd_t* h, const float* corr) {
     return fail(h, LBMHD_ERR_INVALID, "the subgrid correction needs binary64 or binary32 storage");
   if (corr && h->closure) return fail(h, LBMHD_ERR_INVALID, "detach the learned closure first");
   h->corr_static = corr;
+  drop_graphs(h);
   return LBMHD_OK;
 }
 
@@ -549,8 +547,10 @@ int lbmhd_set_closure(lbmhd_t* h, lbmhd_closure_t* c) {
     }
     // the closure's parameters must be in place before this handle's stream reads them
     LB_CUDA(h, cudaStreamSynchronize(closure_stream(c)));
+    LB_CUDA(h, prepare_closure_kernels());  // before any graph capture
   }
   h->closure = c;
+  drop_graphs(h);
   return LBMHD_OK;
 }
 

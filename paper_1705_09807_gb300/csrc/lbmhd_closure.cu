@@ -561,18 +561,25 @@ int net_grid(int batch, int H, int W, int num_sms) {
 }
 
 template <int SRC>
-cudaError_t launch_net_impl(const void* src, const StepGeom& g, const float* in_scale, const unsigned char* packed,
-                            const float* oscale, int batch, int H, int W, float* out, unsigned* err,
-                            cudaStream_t s) {
-  int dev = 0, sms = 152;
+cudaError_t set_net_attributes() {
+  int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   static bool attr_set[64] = {};
-  if (dev < 64 && !attr_set[dev]) {
-    e = cudaFuncSetAttribute(net_tc_kernel<SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNetSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr_set[dev] = true;
-  }
+  if (dev < 64 && attr_set[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(net_tc_kernel<SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNetSmemBytes);
+  if (e == cudaSuccess && dev < 64) attr_set[dev] = true;
+  return e;
+}
+
+template <int SRC>
+cudaError_t launch_net_impl(const void* src, const StepGeom& g, const float* in_scale, const unsigned char* packed,
+                            const float* oscale, int batch, int H, int W, float* out, unsigned* err,
+                            cudaStream_t s) {
+  cudaError_t e = set_net_attributes<SRC>();
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   net_tc_kernel<SRC><<<net_grid(batch, H, W, sms), kNetThreads, kNetSmemBytes, s>>>(src, g, in_scale, packed, oscale,
                                                                                     batch, H, W, out, err);
@@ -698,6 +705,12 @@ int grid_for(long n) {
 }  // namespace
 
 int closure_num_params() { return kNumParams; }
+
+cudaError_t prepare_closure_kernels() {
+  cudaError_t e = set_net_attributes<1>();
+  if (e == cudaSuccess) e = set_net_attributes<2>();
+  return e;
+}
 
 // Correction planes [4][m][m] (physical units) for the current populations of a square
 // binary64 / binary32 grid: one launch of the fused network kernel (pull, u and B, features,

@@ -27,6 +27,7 @@ struct lbmhd {
   bool own_stream = false;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;  // ordering with the legacy default stream
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  long graph_launches = 0;  // kernel launches in one captured graph
   CUtensorMap tmap[2];             // 3-D TMA descriptors of the two copies
   unsigned* err_flag = nullptr;    // device word: set by the step kernel on a pipeline timeout
   void* spec_work = nullptr;       // spectrum work buffer and outputs (allocated on first use)

@@ -150,6 +150,8 @@ cudaError_t launch_energy_spectrum(const double* ux, const double* uy, const dou
 int closure_num_params();
 cudaError_t closure_correction(const lbmhd_closure_t* c, int precision, const void* pops, const StepGeom& g,
                                float* corr, unsigned* err, cudaStream_t s);
+// Kernel attributes of the network kernels (shared-memory size); call outside stream capture.
+cudaError_t prepare_closure_kernels();
 
 const float* closure_device_params(const lbmhd_closure_t* c);
 const float* closure_device_scales(const lbmhd_closure_t* c);
