@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--precision", choices=["fp16", "fp32", "fp64"], default="fp32")
     ap.add_argument("--delta", type=float, default=0.0)
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--only", choices=["closure", "ensemble"],
+                    help="run one side measurement alone and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -503,6 +505,14 @@ def run_reference(a, rank, ws):
 
 def main():
     a = parse()
+    if a.only:
+        import torch
+        torch.cuda.init()
+        from paper_1705_09807_gb300 import build
+        build.build()
+        res = learned_closure_rate(a.steps) if a.only == "closure" else ensemble_measurement(a.steps)
+        print(json.dumps(res), flush=True)
+        return
     if a.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         ws = int(os.environ.get("WORLD_SIZE", "1"))

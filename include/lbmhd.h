@@ -215,14 +215,18 @@ int lbmhd_closure_gradient(lbmhd_closure_t* c, const float* x, const float* t, i
 int lbmhd_closure_train_step(lbmhd_closure_t* c, const float* x, const float* t, int batch, int h,
                              int w, float lr, double* loss);
 /* Network output (scaled units) for device features x into out [batch][4][h][w]:
- * tensor_cores = 1 uses the bf16 mma path, 0 the binary32 path.  Synchronises. */
+ * tensor_cores = 1 runs the fused bf16 tcgen05 kernel (all three layers in one launch, fp32
+ * accumulation in tensor memory), 0 the binary32 layer-by-layer kernels.  Synchronises;
+ * LBMHD_ERR_TIMEOUT if a tensor-core completion wait of the fused kernel ran out (2 s). */
 int lbmhd_closure_forward(lbmhd_closure_t* c, const float* x, int batch, int h, int w, float* out,
                           int tensor_cores);
 const char* lbmhd_closure_last_error(const lbmhd_closure_t* c);
 void lbmhd_closure_free(lbmhd_closure_t* c);
 /* Attach a closure to a square binary64 / binary32 handle (NULL detaches): every step then runs
- * moments -> features -> network (tensor cores) -> correction -> fused step.  The closure must
- * outlive the attachment and must not be trained while attached. */
+ * two launches, the fused network kernel (pull of the populations, u and B and the features in
+ * binary32, the three tcgen05 layers, output scale -> correction planes) and the corrected fused
+ * step; on the handle's own stream whole groups of 32 steps run as one CUDA graph.  The closure
+ * must outlive the attachment and must not be trained while attached. */
 int lbmhd_set_closure(lbmhd_t* h, lbmhd_closure_t* c);
 
 /* Failure-detection test hook.  With enable = 1, the first block of every following step
