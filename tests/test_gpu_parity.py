@@ -166,11 +166,11 @@ def test_fp32_short_runs_elementwise(nx, ny, stencil):
     assert np.max(np.abs(pops - ref)) < 2e-7
 
 
-def _sampled_full_size(n, precision, delta, nu, warm, tol, seed=1):
+def _sampled_full_size(n, precision, delta, nu, warm, tol, seed=1, delta_frac=1 / 32):
     """Full-size grid in the benchmark's launch configuration: after `warm` steps, one more GPU
     step must equal the oracle's single-cell collision of the GPU's own state at sampled cells
     (f_i(x + c_i) after the step = f*_i(x) from the state before it)."""
-    fields = kh_jet(n, seed=seed)
+    fields = kh_jet(n, delta_frac=delta_frac, seed=seed)
     s, sm = oracle.srt_rates(nu), oracle.rate_from_diffusivity(nu)
     p = lbmhd.make_params(n, n, s, sm, delta, precision)
     with lbmhd.Lbmhd(p, *fields) as sim:
@@ -212,3 +212,12 @@ def test_full_size_2048_fp16_les_sampled():
 @pytest.mark.slow
 def test_full_size_2048_fp64_les_sampled():
     _sampled_full_size(2048, lbmhd.LBMHD_FP64, 2.0, 5e-4, 20, 1e-15)
+
+
+# The 4096^2 precision configuration (KH jet with d = N/64, nu = eta = 2e-4, Delta = 2) in all
+# three storage forms; tolerances as for 2048^2.
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,warm,tol", [(lbmhd.LBMHD_FP64, 10, 1e-15), (lbmhd.LBMHD_FP32, 30, 1e-7),
+                                                (lbmhd.LBMHD_FP16, 30, 1e-4)])
+def test_full_size_4096_precision_config_sampled(precision, warm, tol):
+    _sampled_full_size(4096, precision, 2.0, 2e-4, warm, tol, seed=3, delta_frac=1 / 64)
