@@ -55,6 +55,12 @@ __host__ __device__ constexpr int index_in_group(int i) {
 __host__ __device__ constexpr int plane_of(int q) {
   return 9 * group_of(q % 9) + 3 * (q / 9) + index_in_group(q % 9);
 }
+// Inverse of plane_of: the population index q stored in plane pl.
+__host__ __device__ constexpr int q_of_plane(int pl) {
+  int q = 0;
+  while (plane_of(q) != pl) ++q;
+  return q;
+}
 __host__ __device__ constexpr double lattice_w(int i) {
   return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
