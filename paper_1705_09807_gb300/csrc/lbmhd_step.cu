@@ -149,6 +149,127 @@ __device__ __forceinline__ void collide(T p[kQ], T rho1, T jx, T jy, T bx, T by,
 }
 
 
+// ---- packed binary32 pairs (two cells per thread, binary16 storage) ---------------------------
+// Blackwell executes add / sub / mul / fma on two binary32 lanes held in a 64-bit register pair
+// as one instruction (PTX .f32x2, round to nearest on each lane).  F2 holds (cell a, cell b).
+struct F2 {
+  uint64_t v;
+};
+__device__ __forceinline__ F2 f2(float a, float b) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ F2 f2(float a) { return f2(a, a); }
+__device__ __forceinline__ float lo(F2 x) { return __uint_as_float((uint32_t)x.v); }
+__device__ __forceinline__ float hi(F2 x) { return __uint_as_float((uint32_t)(x.v >> 32)); }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
+  F2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+  F2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) {
+  F2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+// a * b + c, one rounding per lane
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
+  F2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+
+struct KCoef2 {
+  F2 r3, r4, r5, r6, r7, r8, sm, kq;
+};
+__device__ __forceinline__ KCoef2 pair_coef(const KCoef<float>& c) {
+  return {f2(c.r3), f2(c.r4), f2(c.r5), f2(c.r6), f2(c.r7), f2(c.r8), f2(c.sm), f2(c.kq)};
+}
+
+// `collide` for two cells at once (same equations and operation order per lane, with the
+// products that the scalar form leaves to the compiler's contraction written as fma).
+__device__ __forceinline__ void collide_pair(F2 p[kQ], F2 rho1, F2 jx, F2 jy, F2 bx, F2 by, const F2 dJ[4],
+                                             const F2 dB[4], const KCoef2& c) {
+  const F2 one = f2(1.f), two = f2(2.f), three = f2(3.f), four = f2(4.f), five = f2(5.f);
+  const F2 r = one + rho1;
+  const F2 ir = f2(1.f / lo(r), 1.f / hi(r));
+  const F2 k = c.kq;
+  const F2 Gxx = fma2(dJ[1], dJ[1], dJ[0] * dJ[0]);
+  const F2 Gyy = fma2(dJ[3], dJ[3], dJ[2] * dJ[2]);
+  const F2 Gxy = fma2(dJ[1], dJ[3], dJ[0] * dJ[2]);
+  const F2 Hxx = fma2(dB[1], dB[1], dB[0] * dB[0]);
+  const F2 Hyy = fma2(dB[3], dB[3], dB[2] * dB[2]);
+  const F2 Hxy = fma2(dB[1], dB[3], dB[0] * dB[2]);
+  const F2 Kxy = fma2(dJ[1], dB[3], dJ[0] * dB[2]);
+  const F2 Kyx = fma2(dJ[3], dB[1], dJ[2] * dB[0]);
+  const F2 Qxx = fma2(k, Gxx, jx * jx) * ir;
+  const F2 Qyy = fma2(k, Gyy, jy * jy) * ir;
+  const F2 Qxy = fma2(k, Gxy, jx * jy) * ir;
+  const F2 Rxx = fma2(k, Hxx, bx * bx);
+  const F2 Ryy = fma2(k, Hyy, by * by);
+  const F2 Rxy = fma2(k, Hxy, bx * by);
+  const F2 E = fma2(k, Kxy - Kyx, jx * by - jy * bx) * ir;
+
+  const F2 a13 = p[1] + p[3], a24 = p[2] + p[4], a57 = p[5] + p[7], a68 = p[6] + p[8];
+  const F2 qq = Qxx + Qyy;
+  const F2 n3 = (a57 - a68) - (Qxy - Rxy);
+  const F2 n4 = (a13 - a24) - ((Qxx - Qyy) - (Rxx - Ryy));
+  const F2 n5 = fma2(two, p[3] - p[1], (p[5] - p[6]) + (p[8] - p[7])) + jx;
+  const F2 n6 = fma2(two, p[4] - p[2], (p[5] - p[8]) + (p[6] - p[7])) + jy;
+  const F2 n7 = fma2(three, qq, fma2(four, a57 + a68, fma2(four, p[0], f2(-5.f) * (a13 + a24))));
+  const F2 n8 = fma2(three, qq, fma2(f2(-5.f / 3.f), rho1, four * p[0] - (a57 + a68)));
+  const F2 d3 = c.r3 * n3, d4 = c.r4 * n4, d5 = c.r5 * n5, d6 = c.r6 * n6, d7 = c.r7 * n7, d8 = c.r8 * n8;
+  const F2 e78 = fma2(f2(-4.f), d7, d8);
+  p[0] = fma2(f2(-4.f), d7 + d8, p[0]);
+  const F2 u = five * d7 - d4, w = fma2(five, d7, d4);
+  p[1] = p[1] + fma2(two, d5, u);
+  p[3] = p[3] + fma2(f2(-2.f), d5, u);
+  p[2] = p[2] + fma2(two, d6, w);
+  p[4] = p[4] + fma2(f2(-2.f), d6, w);
+  p[5] = p[5] + (e78 - ((d3 + d5) + d6));
+  p[6] = p[6] + (e78 + ((d3 + d5) - d6));
+  p[7] = p[7] + (e78 + ((d5 + d6) - d3));
+  p[8] = p[8] + (e78 + ((d3 + d6) - d5));
+
+  const F2 sm = c.sm;
+  const F2 e3 = three * E;
+  const F2 wa = f2(1.f / 9.f), wd = f2(1.f / 36.f);
+  {
+    const F2 bm = bx - e3, bp = bx + e3;
+    const F2 ea = wa * bx, em = wa * bm, ep = wa * bp, dm = wd * bm, dp = wd * bp;
+    const F2 e0 = bx - (((ea + ea) + (em + ep)) + ((dm + dm) + (dp + dp)));
+    p[9] = fma2(sm, e0 - p[9], p[9]);
+    p[10] = fma2(sm, ea - p[10], p[10]);
+    p[11] = fma2(sm, em - p[11], p[11]);
+    p[12] = fma2(sm, ea - p[12], p[12]);
+    p[13] = fma2(sm, ep - p[13], p[13]);
+    p[14] = fma2(sm, dm - p[14], p[14]);
+    p[15] = fma2(sm, dm - p[15], p[15]);
+    p[16] = fma2(sm, dp - p[16], p[16]);
+    p[17] = fma2(sm, dp - p[17], p[17]);
+  }
+  {
+    const F2 bp = by + e3, bm = by - e3;
+    const F2 ea = wa * by, ep = wa * bp, em = wa * bm, dp = wd * bp, dm = wd * bm;
+    const F2 e0 = by - (((ea + ea) + (em + ep)) + ((dm + dm) + (dp + dp)));
+    p[18] = fma2(sm, e0 - p[18], p[18]);
+    p[19] = fma2(sm, ep - p[19], p[19]);
+    p[20] = fma2(sm, ea - p[20], p[20]);
+    p[21] = fma2(sm, em - p[21], p[21]);
+    p[22] = fma2(sm, ea - p[22], p[22]);
+    p[23] = fma2(sm, dp - p[23], p[23]);
+    p[24] = fma2(sm, dm - p[24], p[24]);
+    p[25] = fma2(sm, dm - p[25], p[25]);
+    p[26] = fma2(sm, dp - p[26], p[26]);
+  }
+}
+
 // Arithmetic type for each storage type: binary16 populations are collided in binary32.
 template <typename S> struct ArithOf { using type = S; };
 template <> struct ArithOf<__half> { using type = float; };
@@ -162,8 +283,13 @@ struct StepSmem {
   static constexpr int kGroupElems = ((9 * kBoxW * (int)sizeof(S) + 127) / 128 * 128) / (int)sizeof(S);
   static constexpr int kStageElems = 3 * kGroupElems;
   static constexpr uint32_t kTxBytes = 3u * 9u * kBoxW * sizeof(S);  // bytes landing per stage
+  // moment ring row: the strip's columns plus one halo column each side; binary16 (two cells
+  // per thread) keeps the strip at an even offset (column c at c + 2) so a cell pair is 8-byte
+  // aligned
+  static constexpr int kRingW = sizeof(S) == 2 ? kStepThreads + 4 : kStepThreads + 2;
+  static constexpr int kRingOff = sizeof(S) == 2 ? 2 : 1;  // ring index of strip column 0
   S stage[NST][kStageElems];
-  C ring[kRing][4][kStepThreads + 2];
+  C ring[kRing][4][kRingW];
   uint64_t full[NST];
   int abort_flag[2];
 };
@@ -231,6 +357,7 @@ __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict_
   constexpr int BW = SM::kBoxW;
   SM& S_ = step_smem<S, NST>();
 
+  static_assert(SM::kRingOff == 1, "one cell per thread: strip column c at ring index c + 1");
   const int t = threadIdx.x;
   const int nx = g.nx, ny = g.ny;
   const int ncol = min(kStepThreads, nx - x0);
@@ -269,7 +396,7 @@ __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict_
   auto ring_moments = [&](int k) {
     const S* st = S_.stage[slot(k)];
     T* rg = &S_.ring[k & (kRing - 1)][0][0];
-    constexpr int RS = kStepThreads + 2;
+    constexpr int RS = SM::kRingW;
     T r1, jx, jy, bx, by;
     if (active) {
       moments_from<T, S, BW>(st, GE, t + LEAD, r1, jx, jy, bx, by);
@@ -332,7 +459,7 @@ __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict_
     }
     // C: gradients, collision and store of row m
     if (active) {
-      constexpr int RS = kStepThreads + 2;
+      constexpr int RS = SM::kRingW;
       const T* rc = &S_.ring[m & (kRing - 1)][0][0];
       const T* rn = &S_.ring[(dir > 0 ? m + 1 : m - 1) & (kRing - 1)][0][0];  // row y + 1
       const T* rs = &S_.ring[(dir > 0 ? m - 1 : m + 1) & (kRing - 1)][0][0];  // row y - 1
@@ -394,17 +521,254 @@ __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict_
   return true;
 }
 
+// The pair (staged value of population q at box columns col, col + 1) for two adjacent cells.
+template <int BW>
+__device__ __forceinline__ F2 staged_pair(const __half* st, int ge, int q, int col) {
+  const int i = q % 9;
+  const __half* a = st + group_of(i) * ge + (3 * (q / 9) + index_in_group(i)) * BW + col - vel_x(i);
+  if (vel_x(i) == 0) {  // even column: one aligned 32-bit load
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(a));
+    return f2(v.x, v.y);
+  }
+  return f2(__half2float(a[0]), __half2float(a[1]));
+}
+
+template <int BW>
+__device__ __forceinline__ void moments_pair(const __half* st, int ge, int col, F2& rho1, F2& jx, F2& jy, F2& bx,
+                                             F2& by) {
+  auto v = [&](int q) -> F2 { return staged_pair<BW>(st, ge, q, col); };
+  const F2 f0 = v(0), f1 = v(1), f2_ = v(2), f3 = v(3), f4 = v(4), f5 = v(5), f6 = v(6), f7 = v(7), f8 = v(8);
+  rho1 = ((f0 + f1) + (f2_ + f3)) + ((f4 + f5) + (f6 + f7)) + f8;
+  jx = (f1 - f3) + (f5 - f6) + (f8 - f7);
+  jy = (f2_ - f4) + (f5 - f8) + (f6 - f7);
+  bx = ((v(9) + v(10)) + (v(11) + v(12))) + ((v(13) + v(14)) + (v(15) + v(16))) + v(17);
+  by = ((v(18) + v(19)) + (v(20) + v(21))) + ((v(22) + v(23)) + (v(24) + v(25))) + v(26);
+}
+
+// Store the 27 values of two adjacent cells (binary16 pairs, one 32-bit store per plane), planes
+// in address order; `both` false stores the first cell only (odd strip width).
+template <int PL>
+__device__ __forceinline__ void store_planes_pair(__half* op, const F2* p, size_t plane, bool both) {
+  if constexpr (PL < kQ) {
+    constexpr int q = q_of_plane(PL);
+    if (both)
+      *reinterpret_cast<__half2*>(op) = __floats2half2_rn(lo(p[q]), hi(p[q]));
+    else
+      *op = __float2half_rn(lo(p[q]));
+    store_planes_pair<PL + 1>(op + plane, p, plane, both);
+  }
+}
+
+// One tile of a binary16 grid with two adjacent cells per thread (kStepThreads / 2 threads per
+// strip of kStepThreads columns): the pipeline of run_tile, with the moments, the collision
+// and the stores of a cell pair in packed binary32 (F2).  Same arguments and contract as run_tile.
+template <int ISO, int NST>
+__device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* __restrict__ dst, const StepGeom& g,
+                                              const KCoef<float>& c1, int x0, int y0, int band_parity,
+                                              uint32_t& kbase, unsigned* __restrict__ err) {
+  using SM = StepSmem<__half, NST>;
+  constexpr int GE = SM::kGroupElems;
+  constexpr int LEAD = SM::kLead;
+  constexpr int BW = SM::kBoxW;
+  constexpr int RW = SM::kRingW;
+  static_assert(SM::kRingOff == 2, "pair layout");
+  SM& S_ = step_smem<__half, NST>();
+
+  const int t = threadIdx.x;
+  const int c0 = 2 * t;  // first of this thread's two strip columns
+  const int nx = g.nx, ny = g.ny;
+  const int ncol = min(kStepThreads, nx - x0);
+  const bool active = c0 < ncol;
+  const int last = (ncol - 1) / 2;  // thread holding the strip's last column
+  const int y1 = min(y0 + g.band, ny);
+  const int L = (y1 - y0) + 2;
+  const int dir = (band_parity & 1) ? -1 : 1;
+  const uint32_t kb = kbase;
+  const KCoef2 c = pair_coef(c1);
+  auto row_of = [&](int k) -> int {
+    int r = dir > 0 ? y0 - 1 + k : y1 - k;
+    if (r < 0) r += ny;
+    if (r >= ny) r -= ny;
+    return r;
+  };
+  auto issue = [&](int k) {
+    if (g.skip_copy && k == 2 && blockIdx.x == 0 && blockIdx.y == 0) return;  // test hook
+    const uint32_t K = kb + (uint32_t)k;
+    const int s = (int)(K % NST);
+    const int r = row_of(k);
+    const int ra = r == 0 ? ny - 1 : r - 1;
+    const int rc = r == ny - 1 ? 0 : r + 1;
+    const int cx = x0 + kXOff - LEAD;
+    mbar_arrive_expect_tx(&S_.full[s], SM::kTxBytes);
+    tma_load_3d(&S_.stage[s][0], srcp, cx, ra, 0, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][GE], srcp, cx, r, 9, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][2 * GE], srcp, cx, rc, 18, &S_.full[s]);
+  };
+  auto slot = [&](int k) -> int { return (int)((kb + (uint32_t)k) % NST); };
+  auto wait_row = [&](int k) -> bool {
+    const uint32_t K = kb + (uint32_t)k;
+    return mbar_wait_bounded(&S_.full[K % NST], (K / NST) & 1u, kWaitLimitNs);
+  };
+  // moments of staged row k into ring slot k & 3: the thread's cell pair at ring index c0 + 2,
+  // the halo columns -1 (index 1) and ncol (index ncol + 2; covered by the last pair when ncol
+  // is odd)
+  F2 rho_next = f2(0.f);
+  auto ring_moments = [&](int k) {
+    const __half* st = S_.stage[slot(k)];
+    float* rg = &S_.ring[k & (kRing - 1)][0][0];
+    if (active) {
+      F2 r1, jx, jy, bx, by;
+      moments_pair<BW>(st, GE, c0 + LEAD, r1, jx, jy, bx, by);
+      *reinterpret_cast<uint64_t*>(rg + 0 * RW + c0 + 2) = jx.v;
+      *reinterpret_cast<uint64_t*>(rg + 1 * RW + c0 + 2) = jy.v;
+      *reinterpret_cast<uint64_t*>(rg + 2 * RW + c0 + 2) = bx.v;
+      *reinterpret_cast<uint64_t*>(rg + 3 * RW + c0 + 2) = by.v;
+      rho_next = r1;
+    }
+    float r1, jx, jy, bx, by;
+    if (t == 0) {
+      moments_from<float, __half, BW>(st, GE, LEAD - 1, r1, jx, jy, bx, by);
+      rg[0 * RW + 1] = jx;
+      rg[1 * RW + 1] = jy;
+      rg[2 * RW + 1] = bx;
+      rg[3 * RW + 1] = by;
+    }
+    if (t == last && (ncol & 1) == 0) {
+      moments_from<float, __half, BW>(st, GE, ncol + LEAD, r1, jx, jy, bx, by);
+      rg[0 * RW + ncol + 2] = jx;
+      rg[1 * RW + ncol + 2] = jy;
+      rg[2 * RW + ncol + 2] = bx;
+      rg[3 * RW + ncol + 2] = by;
+    }
+  };
+
+  if (t == 0) {
+    S_.abort_flag[0] = 0;
+    S_.abort_flag[1] = 0;
+  }
+  __syncthreads();
+  const int first = NST < L ? NST : L;
+  if (t == 0) {
+    fence_proxy_async_smem();
+    for (int k = 0; k < first; ++k) issue(k);
+  }
+  int issued = first;
+
+  if (wait_row(0)) ring_moments(0); else S_.abort_flag[1] = 1;
+  if (wait_row(1)) ring_moments(1); else S_.abort_flag[1] = 1;
+  F2 rho_cur = rho_next;
+
+  const size_t pitch = (size_t)g.pitch;
+  for (int m = 1; m <= L - 2; ++m) {
+    if (wait_row(m + 1)) ring_moments(m + 1); else S_.abort_flag[m & 1] = 1;
+    __syncthreads();
+    if (S_.abort_flag[m & 1]) {
+      if (t == 0) {
+        atomicOr(err, 1u);
+        for (int k = m + 1; k < issued; ++k) wait_row(k);
+      }
+      return false;
+    }
+    if (t == 0 && m - 1 + NST < L) {
+      fence_proxy_async_smem();
+      issue(m - 1 + NST);
+      ++issued;
+    }
+    if (active) {
+      const float* rc = &S_.ring[m & (kRing - 1)][0][0];
+      const float* rn = &S_.ring[(dir > 0 ? m + 1 : m - 1) & (kRing - 1)][0][0];
+      const float* rs = &S_.ring[(dir > 0 ? m - 1 : m + 1) & (kRing - 1)][0][0];
+      const int si = c0 + 2;  // ring index of the first cell
+      F2 dJ[4], dB[4], own[4];
+      if (ISO) {
+        // per cell as in run_tile: 4 (a_E - a_W) + (a_NE - a_NW) + (a_SE - a_SW), etc.
+        F2 dx[4], dy[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          float ddx[2], ddy[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = si + h;
+            const float e = rc[f * RW + j + 1], w = rc[f * RW + j - 1];
+            const float ne = rn[f * RW + j + 1], nw = rn[f * RW + j - 1], nn = rn[f * RW + j];
+            const float se = rs[f * RW + j + 1], sw = rs[f * RW + j - 1], ss = rs[f * RW + j];
+            ddx[h] = 4.f * (e - w) + ((ne - nw) + (se - sw));
+            ddy[h] = 4.f * (nn - ss) + ((ne - se) + (nw - sw));
+          }
+          dx[f] = f2(ddx[0], ddx[1]);
+          dy[f] = f2(ddy[0], ddy[1]);
+          own[f].v = *reinterpret_cast<const uint64_t*>(rc + f * RW + si);
+        }
+        dJ[0] = dx[0]; dJ[1] = dy[0]; dJ[2] = dx[1]; dJ[3] = dy[1];
+        dB[0] = dx[2]; dB[1] = dy[2]; dB[2] = dx[3]; dB[3] = dy[3];
+      } else {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          own[f].v = *reinterpret_cast<const uint64_t*>(rc + f * RW + si);
+          F2 nrow, srow;
+          nrow.v = *reinterpret_cast<const uint64_t*>(rn + f * RW + si);
+          srow.v = *reinterpret_cast<const uint64_t*>(rs + f * RW + si);
+          const F2 ddx = f2(hi(own[f]) - rc[f * RW + si - 1], rc[f * RW + si + 2] - lo(own[f]));
+          const F2 ddy = nrow - srow;
+          if (f < 2) { dJ[2 * f] = ddx; dJ[2 * f + 1] = ddy; }
+          else { dB[2 * (f - 2)] = ddx; dB[2 * (f - 2) + 1] = ddy; }
+        }
+      }
+      const __half* st = S_.stage[slot(m)];
+      F2 p[kQ];
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) p[q] = staged_pair<BW>(st, GE, q, c0 + LEAD);
+      collide_pair(p, rho_cur, own[0], own[1], own[2], own[3], dJ, dB, c);
+      const int y = row_of(m);
+      const int x = x0 + c0;
+      __half* o = dst + (size_t)y * pitch + kXOff + x;
+      store_planes_pair<0>(o, p, g.plane, c0 + 1 < ncol);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int xh = x + h;
+        if (h == 1 && c0 + 1 >= ncol) break;
+        if (xh < 2 || xh >= nx - 2) {  // ghosts: logical nx, nx + 1 and -2, -1
+          __half* gp = o + h + (xh < 2 ? nx : -nx);
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) gp[(size_t)plane_of(q) * g.plane] = __float2half_rn(h ? hi(p[q]) : lo(p[q]));
+        }
+      }
+    }
+    rho_cur = rho_next;
+  }
+  kbase = kb + (uint32_t)L;
+  return true;
+}
+
+// Threads of a step block: one per strip column, or one per column pair for binary16 storage.
+template <typename S>
+__host__ __device__ constexpr int step_threads() {
+  return sizeof(S) == 2 ? kStepThreads / 2 : kStepThreads;
+}
+
+// One tile of the strip starting at x0 (binary16: two cells per thread).
+template <typename S, int ISO, int NST, bool CORR = false>
+__device__ __forceinline__ bool run_any_tile(const CUtensorMap* srcp, S* __restrict__ dst, const StepGeom& g,
+                                             const KCoef<typename ArithOf<S>::type>& c, int x0, int y0,
+                                             int band_parity, uint32_t& kbase, unsigned* __restrict__ err,
+                                             const float* __restrict__ corr = nullptr) {
+  if constexpr (sizeof(S) == 2)
+    return run_tile_pair<ISO, NST>(srcp, dst, g, c, x0, y0, band_parity, kbase, err);
+  else
+    return run_tile<S, ISO, NST, CORR>(srcp, dst, g, c, x0, y0, band_parity, kbase, err, corr);
+}
+
 // One grid: block (strip, band) = one tile.  CORR: add the correction planes corr[4][ny][nx].
 template <typename S, int ISO, int NST, int MINB, bool CORR = false>
-__global__ void __launch_bounds__(kStepThreads, MINB)
+__global__ void __launch_bounds__(step_threads<S>(), MINB)
     fused_step_kernel(const __grid_constant__ CUtensorMap src, S* __restrict__ dst, StepGeom g,
                       KCoef<typename ArithOf<S>::type> c, unsigned* __restrict__ err,
                       const float* __restrict__ corr) {
   if ((int)blockIdx.y * g.band >= g.ny) return;  // uniform per block
   init_stage_barriers(step_smem<S, NST>(), &src);
   uint32_t kbase = 0;
-  run_tile<S, ISO, NST, CORR>(&src, dst, g, c, blockIdx.x * kStepThreads, blockIdx.y * g.band,
-                              blockIdx.y, kbase, err, corr);
+  run_any_tile<S, ISO, NST, CORR>(&src, dst, g, c, blockIdx.x * kStepThreads, blockIdx.y * g.band, blockIdx.y,
+                                  kbase, err, corr);
 }
 
 // Ensemble: every member grid advances one step in this launch.  work[i] = {member, x0, y0,
@@ -419,7 +783,7 @@ struct EnsembleMember {
 };
 
 template <typename S, int ISO, int NST, int MINB>
-__global__ void __launch_bounds__(kStepThreads, MINB)
+__global__ void __launch_bounds__(step_threads<S>(), MINB)
     ensemble_step_kernel(const EnsembleMember<S>* __restrict__ members, const int4* __restrict__ work,
                          int nwork, int parity, unsigned long long* queue, unsigned* __restrict__ err) {
   __shared__ int next_item;
@@ -434,8 +798,8 @@ __global__ void __launch_bounds__(kStepThreads, MINB)
   while (w < nwork) {
     const int4 it = work[w];
     const EnsembleMember<S>& mb = members[it.x];
-    if (!run_tile<S, ISO, NST>(&mb.map[parity], mb.pops[parity ^ 1], mb.g, mb.c, it.y, it.z, it.w,
-                               kbase, err))
+    if (!run_any_tile<S, ISO, NST>(&mb.map[parity], mb.pops[parity ^ 1], mb.g, mb.c, it.y, it.z, it.w,
+                                   kbase, err))
       return;
     if (queue) {
       __syncthreads();  // everyone has read next_item before it is overwritten
@@ -462,13 +826,15 @@ KCoef<T> cast_coef(const StepCoef& c) {
   return k;
 }
 
-// Pipeline depth and residency per storage type.  binary32 rows are 15 KB per stage: 3 stages
-// (one row in flight) and 4 blocks per SM (16 warps, 128 registers) measured fastest at 2048^2
-// and 4096^2 -- more resident warps beat deeper pipelines (4 stages x 3 blocks: 0.81 of the
-// copy bandwidth, 3 x 4: 0.92).  binary16 rows are 8 KB and that form is bound by instruction
-// issue rather than memory (about 40 GLUPS for any depth/residency tried); 3 stages x 6 blocks
-// (76 registers) measured best.  binary64 rows are 30 KB: 3 stages, 2 blocks per SM; that form
-// is bound by the binary64 arithmetic rate.  Overridable at build time for sweeps.
+// Pipeline depth and residency per storage type (at least 3 stages: iteration m waits for row
+// m + 1, which must already have been issued).  binary32 rows are 15 KB per stage: 3 stages and
+// 4 blocks per SM (16 warps) measured fastest at 2048^2 and 4096^2 -- more resident warps beat
+// deeper pipelines (4 stages x 3 blocks: 0.81 of the copy bandwidth, 3 x 4: 0.92).  binary16
+// rows are 8 KB; that form runs two cells per thread (64-thread blocks, packed binary32
+// arithmetic) and is bound by latency at the 12 warps per SM that shared memory allows: 3
+// stages x 6 blocks measured best at 2048^2 (46.4 GLUPS; 5 x 4: 43.4, 4 x 5: 40.0, 3 x 5: 39.8).
+// binary64 rows are 30 KB: 3 stages, 2 blocks per SM; that form is bound by the binary64
+// arithmetic rate.  Overridable at build time for sweeps.
 #ifndef LBMHD_F32_STAGES
 #define LBMHD_F32_STAGES 3
 #endif
@@ -520,14 +886,14 @@ cudaError_t launch_step(const CUtensorMap& src, S* dst, const StepGeom& g, const
     if constexpr (sizeof(S) == 2) {
       return cudaErrorNotSupported;  // the correction is offered for binary64 / binary32 storage
     } else if (stencil == 1) {
-      kernel_ptr<S, 1, true>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(src, dst, g, k, err, corr);
+      kernel_ptr<S, 1, true>()<<<grid, step_threads<S>(), smem_bytes<S>(), s>>>(src, dst, g, k, err, corr);
     } else {
-      kernel_ptr<S, 0, true>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(src, dst, g, k, err, corr);
+      kernel_ptr<S, 0, true>()<<<grid, step_threads<S>(), smem_bytes<S>(), s>>>(src, dst, g, k, err, corr);
     }
   } else if (stencil == 1) {
-    kernel_ptr<S, 1>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(src, dst, g, k, err, nullptr);
+    kernel_ptr<S, 1>()<<<grid, step_threads<S>(), smem_bytes<S>(), s>>>(src, dst, g, k, err, nullptr);
   } else {
-    kernel_ptr<S, 0>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(src, dst, g, k, err, nullptr);
+    kernel_ptr<S, 0>()<<<grid, step_threads<S>(), smem_bytes<S>(), s>>>(src, dst, g, k, err, nullptr);
   }
   return cudaGetLastError();
 }
@@ -575,9 +941,9 @@ cudaError_t launch_ens(int stencil, const void* members, const int4* work, int n
                        unsigned long long* queue, int grid, unsigned* err, cudaStream_t s) {
   const EnsembleMember<S>* mb = static_cast<const EnsembleMember<S>*>(members);
   if (stencil == 1)
-    ensemble_kernel_ptr<S, 1>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(mb, work, nwork, parity, queue, err);
+    ensemble_kernel_ptr<S, 1>()<<<grid, step_threads<S>(), smem_bytes<S>(), s>>>(mb, work, nwork, parity, queue, err);
   else
-    ensemble_kernel_ptr<S, 0>()<<<grid, kStepThreads, smem_bytes<S>(), s>>>(mb, work, nwork, parity, queue, err);
+    ensemble_kernel_ptr<S, 0>()<<<grid, step_threads<S>(), smem_bytes<S>(), s>>>(mb, work, nwork, parity, queue, err);
   return cudaGetLastError();
 }
 
