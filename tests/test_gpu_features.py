@@ -170,7 +170,7 @@ def test_argument_errors_on_a_live_handle():
         assert sim.launches == launches + 65 and sim.steps == 65
 
 
-@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32])
+@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32, lbmhd.LBMHD_FP16])
 def test_pipeline_wait_timeout_reported_and_context_usable(precision):
     """Failure detection without a fault: one block leaves out one staged-row copy, so its
     time-bounded mbarrier wait runs out; the step reports LBMHD_ERR_TIMEOUT to the host, the

@@ -148,7 +148,7 @@ def test_fp16_kh_jet_64_against_fp64_oracle(steps, tol_u, tol_b):
     assert rl2(np.stack(mom[3:5]), np.stack(omom[3:5])) < tol_b
 
 
-@pytest.mark.parametrize("nx,ny,stencil", [(300, 70, 0), (33, 17, 1), (3, 3, 0)])
+@pytest.mark.parametrize("nx,ny,stencil", [(300, 70, 0), (33, 17, 1), (3, 3, 0), (129, 20, 0), (257, 9, 1)])
 def test_fp16_short_runs_elementwise(nx, ny, stencil):
     fields = smooth_random_fields(nx, ny, seed=3, amp_u=0.05, amp_b=0.04, amp_rho=0.02)
     s, sm = mrt_rates(0.01), oracle.rate_from_diffusivity(0.015)
