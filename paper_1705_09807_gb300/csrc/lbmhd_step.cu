@@ -43,7 +43,6 @@ namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per mbarrier wait
 
-
 template <typename T>
 struct KCoef {
   T r3, r4, r5, r6, r7, r8, sm, kq;
