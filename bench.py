@@ -225,6 +225,15 @@ def e2e_run(n, precision, delta, k):
     return t1 - t0, nbytes, nbytes
 
 
+def field_errors(m, m64):
+    """Relative L2 differences of (rho, ux, uy, bx, by) from the binary64 fields m64: rho,
+    rho - 1 (the departure from the rest density, which carries the compressive motion), the
+    velocity and the magnetic field."""
+    return {"rho": rel_l2(m[0], m64[0]), "rho_minus_1": rel_l2(m[0] - 1.0, m64[0] - 1.0),
+            "u": rel_l2(np.stack(m[1:3]), np.stack(m64[1:3])),
+            "B": rel_l2(np.stack(m[3:5]), np.stack(m64[3:5]))}
+
+
 def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
@@ -351,13 +360,22 @@ def side_measurements(n, a):
         done = t
         m64 = sims["fp64"].moments()
         for p in ("fp32", "fp16"):
-            m = sims[p].moments()
-            acc.setdefault(p, {})[str(t)] = {
-                "rho": rel_l2(m[0], m64[0]), "u": rel_l2(np.stack(m[1:3]), np.stack(m64[1:3])),
-                "B": rel_l2(np.stack(m[3:5]), np.stack(m64[3:5]))}
+            acc.setdefault(p, {})[str(t)] = field_errors(sims[p].moments(), m64)
     for sim in sims.values():
         sim.free()
     res["precision_rel_l2_vs_fp64_gpu"] = acc
+    # the timed workload itself (binary32, Delta = 0) against the same run in binary64
+    acc = {"workload": workload_name(n, "fp32", a.delta)}
+    sims = {p: make_sim(n, p, a.delta)[0] for p in ("fp64", "fp32")}
+    done = 0
+    for t in (1000, 5000):
+        for sim in sims.values():
+            sim.step(t - done)
+        done = t
+        acc[str(t)] = field_errors(sims["fp32"].moments(), sims["fp64"].moments())
+    for sim in sims.values():
+        sim.free()
+    res["workload_rel_l2_vs_fp64_gpu"] = acc
     msl = rate(make_sim(256, "fp32", 2.0)[0], 4096)
     res["les_256_fp32_delta2"] = {"mlups": round(256 * 256 / msl / 1e3, 2)}
     res["les_256_fp32_delta2_network"] = learned_closure_rate()
