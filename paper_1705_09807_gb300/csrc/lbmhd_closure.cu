@@ -236,7 +236,7 @@ constexpr int kSmSlot = kSmBar + 16;
 constexpr int kNetSmemBytes = kSmSlot + 8 + 128;      // + alignment slack
 constexpr int kMS = kPS + 2;                          // moment grid side for the features: 24
 constexpr uint32_t kTmemCols = 128;                   // 4 M tiles x 32 fp32 columns
-constexpr int kNetThreads = 128;
+constexpr int kNetThreads = 256;  // 8 warps: warps w and w + 4 share TMEM lanes 32 (w % 4) ..
 static_assert(kSmBar % 8 == 0, "mbarrier alignment");
 static_assert(5 * kMS * kMS * 4 <= 4 * kChunkBytes, "moments fit in the layer-1 output buffer");
 static_assert(kPadCells >= kPS + 1, "shifted reads stay inside a chunk");
@@ -310,23 +310,27 @@ __device__ __forceinline__ void issue_layer(uint32_t sbase, int act_off, int w_o
 }
 
 // Epilogue of a hidden layer: tanh(D + b) of this thread's cell in each M tile -> bf16 chunks.
+// Warp w reads TMEM lanes 32 (w % 4) .. (its cells); warps 0-3 take channels 0-15, warps 4-7
+// channels 16-31.
 __device__ __forceinline__ void hidden_epilogue(uint32_t tmem, const float* __restrict__ bias,
                                                 unsigned char* __restrict__ dst) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = warp >> 2;
 #pragma unroll 1
   for (int mt = 0; mt < kMT; ++mt) {
-    uint32_t r[32];
-    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + mt * 32, r);
+    uint32_t r[16];
+    tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + mt * 32 + 16 * half, r);
     tmem_ld_wait();
-    const int cell = mt * 128 + 32 * warp + lane;
-    uint32_t pk[16];
+    const int cell = mt * 128 + 32 * quarter + lane;
+    const float* b = bias + 16 * half;
+    uint32_t pk[8];
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
-      pk[j] = bf16x2(tanh_approx(__uint_as_float(r[2 * j]) + bias[2 * j]),
-                     tanh_approx(__uint_as_float(r[2 * j + 1]) + bias[2 * j + 1]));
+    for (int j = 0; j < 8; ++j)
+      pk[j] = bf16x2(tanh_approx(__uint_as_float(r[2 * j]) + b[2 * j]),
+                     tanh_approx(__uint_as_float(r[2 * j + 1]) + b[2 * j + 1]));
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-      *reinterpret_cast<uint4*>(dst + c * kChunkBytes + (kPadCells + cell) * 16) =
+    for (int c = 0; c < 2; ++c)
+      *reinterpret_cast<uint4*>(dst + (2 * half + c) * kChunkBytes + (kPadCells + cell) * 16) =
           make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
   }
 }
@@ -523,7 +527,7 @@ __global__ void __launch_bounds__(kNetThreads, 2)
     if (tid == 0) issue_layer(sbase, kSmXA, kSmW + kW1Bytes + kW2Bytes, 16, 2, kL3First, kL3Tiles, tmem, bar);
     if (!(ok = wait_layer(bar, phase, true))) break;
 #pragma unroll 1
-    for (int mt = 0; mt < kL3Tiles; ++mt) {
+    for (int mt = 0; mt < kL3Tiles && warp < 4; ++mt) {  // warps 0-3: one cell per lane
       uint32_t r[4];
       tmem_ld4(tmem + ((uint32_t)(32 * warp) << 16) + mt * 16, r);
       tmem_ld_wait();
