@@ -45,8 +45,8 @@ NU = ETA = 2e-3   # see the module docstring
 # 2048^2 workload, from an ncu capture; keyed by the SHA-256 of the kernel source it was taken
 # on, so a changed kernel reports null until it is measured again.
 MEASURED_TRAFFIC = {
-    # profiles/fused_step_fp32_2048.md: (470.41 + 407.85 + 470.43 + 405.51) MB / 2 launches
-    ("d9220523cd593a9b", 2048, "fp32", 0.0): 877.10e6,
+    # profiles/fused_step_fp32_2048.md: (470.33 + 408.10 + 470.43 + 405.41) MB / 2 launches
+    ("cd24b3d843db0cc6", 2048, "fp32", 0.0): 877.14e6,
 }
 
 
