@@ -43,10 +43,11 @@ NU = ETA = 2e-3   # see the module docstring
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the fused FP32 kernel on the
 # 2048^2 workload, from an ncu capture; keyed by the SHA-256 of the kernel source it was taken
-# on, so a changed kernel reports null until it is measured again.
+# on (comments and whitespace removed), so a changed kernel reports null until it is measured
+# again.
 MEASURED_TRAFFIC = {
     # profiles/fused_step_fp32_2048.md: (470.33 + 408.10 + 470.43 + 405.41) MB / 2 launches
-    ("cd24b3d843db0cc6", 2048, "fp32", 0.0): 877.14e6,
+    ("f3cd856b84d2f0c4", 2048, "fp32", 0.0): 877.14e6,
 }
 
 
@@ -65,9 +66,19 @@ def parse():
     return ap.parse_args()
 
 
+def source_hash(text: str) -> str:
+    """SHA-256 (16 hex digits) of C++ source with comments and whitespace removed, so that
+    editing a comment does not orphan a measurement taken on the same code."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    text = "".join(text.split())
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
+
+
 def kernel_hash() -> str:
-    with open(os.path.join(ROOT, "paper_1705_09807_gb300", "csrc", "lbmhd_step.cu"), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    with open(os.path.join(ROOT, "paper_1705_09807_gb300", "csrc", "lbmhd_step.cu")) as fh:
+        return source_hash(fh.read())
 
 
 def workload_name(n, precision, delta):

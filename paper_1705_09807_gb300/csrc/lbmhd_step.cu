@@ -3,10 +3,11 @@
 //   pull-stream -> moments -> gradients -> filtered equilibria -> relax -> store
 // on the GPU with each population read once from HBM and written once.
 //
-// Work decomposition.  A block of kStepThreads threads owns a strip of that many adjacent
-// columns and a band of rows; each thread owns one column and the block marches through the
-// band row by row (adjacent bands march in opposite directions, so the two rows a band shares
-// with its neighbour are fetched by both at about the same time and the second fetch hits L2).
+// Work decomposition.  A block owns a strip of kStepThreads adjacent columns and a band of
+// rows; each thread owns one column (binary16 storage: two adjacent columns, whose arithmetic
+// runs in packed binary32 pairs, see run_tile_pair) and the block marches through the band row
+// by row (adjacent bands march in opposite directions, so the two rows a band shares with its
+// neighbour are fetched by both at about the same time and the second fetch hits L2).
 // Rows are staged in shared memory by the tensor-memory accelerator: one elected thread
 // issues, per pulled row r, three 3-D box copies (cp.async.bulk.tensor) of 9 planes x the strip
 // columns each -- source rows r-1, r, r+1 of the three plane groups (planes are grouped by
