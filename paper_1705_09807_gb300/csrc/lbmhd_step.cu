@@ -851,6 +851,13 @@ KCoef<T> cast_coef(const StepCoef& c) {
 #ifndef LBMHD_WAVES
 #define LBMHD_WAVES 1
 #endif
+// Fewest rows per band.  Grids too small to fill one wave with long bands (below about
+// 512^2) are bound by the pipeline's fill latency, not by memory, so thin bands pay: with one
+// row at least, 128^2 binary32 runs at 5.4 GLUPS (4 rows: 2.9), 256^2 at 13.5 (11.8), 256^2
+// binary16 at 14.2 (9.0) and the 64^2 binary64 run at 0.28 (0.10); 512^2 and up are unchanged.
+#ifndef LBMHD_MIN_BAND
+#define LBMHD_MIN_BAND 1
+#endif
 #ifndef LBMHD_F16_STAGES
 #define LBMHD_F16_STAGES 3
 #endif
@@ -1003,7 +1010,8 @@ int resident_step_blocks(int precision, int num_sms) {
 }
 
 // Rows per block: with the blocks that fit on the GPU at once (`resident`), give every strip
-// floor(resident / strips) bands so the whole grid runs in one wave; never fewer than 4 rows.
+// floor(resident / strips) bands so the whole grid runs in one wave; never fewer than
+// LBMHD_MIN_BAND rows.
 int step_band_rows(int nx, int ny, int precision, int num_sms) {
   const int strips = (nx + kStepThreads - 1) / kStepThreads;
   const int per_sm = precision == 0   ? StepConfig<double>::kMinBlocks
@@ -1013,7 +1021,7 @@ int step_band_rows(int nx, int ny, int precision, int num_sms) {
   long bands = resident / strips;
   if (bands < 1) bands = 1;
   long band = (ny + bands - 1) / bands;
-  if (band < 4) band = 4;
+  if (band < LBMHD_MIN_BAND) band = LBMHD_MIN_BAND;
   if (band > ny) band = ny;
   return (int)band;
 }
