@@ -53,7 +53,7 @@ def test_gradient_matches_oracle():
 def test_forward_binary32_and_tensor_cores():
     import torch
     theta = _params(7)
-    x, _ = _batch(b=3, h=16, w=37, seed=9)  # width not a multiple of 16: ragged mma tiles
+    x, _ = _batch(b=3, h=16, w=37, seed=9)  # width not a multiple of 16: ragged 16 x 16 tiles
     xt = torch.tensor(x, dtype=torch.float32, device="cuda")
     ref = oc.forward(theta.astype(np.float32).astype(np.float64), x.astype(np.float32).astype(np.float64))[-1]
     with lbmhd.Closure(theta, IN_SCALE, OUT_SCALE) as cl:
