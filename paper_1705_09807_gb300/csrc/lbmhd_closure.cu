@@ -292,17 +292,24 @@ __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
 }
 
 // Issue one layer: for each M tile, 9 taps x nkc K chunks into TMEM columns mt * n; then commit.
-__device__ __forceinline__ void issue_layer(uint32_t sbase, int act_off, int w_off, int n, int nkc, int first_cell,
-                                            int ntiles, uint32_t tmem, uint64_t* bar) {
-  const uint32_t idesc = idesc_bf16_f32(128, n);
-  for (int mt = 0; mt < ntiles; ++mt) {
+template <int N, int NKC, int FIRST, int NTILES>
+__device__ __forceinline__ void issue_layer(uint32_t sbase, int act_off, int w_off, uint32_t tmem, uint64_t* bar) {
+  // Descriptors of the layer's first A and B operands; every other operand differs only in its
+  // start address, which the descriptor holds in 16-byte units in its low bits (no carry: all
+  // addresses lie inside this CTA's shared memory), so it is the base plus a constant.
+  constexpr uint32_t idesc = idesc_bf16_f32(128, N);
+  const uint64_t a0 = smem_desc(sbase + act_off + (kPadCells + FIRST) * 16, kChunkBytes, 128);
+  const uint64_t b0 = smem_desc(sbase + w_off, 128, 256);
+#pragma unroll
+  for (int mt = 0; mt < NTILES; ++mt) {
+#pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
-      const int shift = (tap / 3 - 1) * kPS + (tap % 3 - 1);
-      const int cell = kPadCells + first_cell + mt * 128 + shift;
-      for (int kc = 0; kc < nkc; ++kc) {
-        const uint64_t a = smem_desc(sbase + act_off + 2 * kc * kChunkBytes + cell * 16, kChunkBytes, 128);
-        const uint64_t b = smem_desc(sbase + w_off + (tap * nkc + kc) * (n * 32), 128, 256);
-        tc_mma_bf16(tmem + mt * n, a, b, idesc, (tap | kc) != 0);
+      const int shift = (tap / 3 - 1) * kPS + (tap % 3 - 1);  // cells
+#pragma unroll
+      for (int kc = 0; kc < NKC; ++kc) {
+        const uint64_t a = a0 + (uint64_t)(int64_t)(mt * 128 + shift + 2 * kc * (kChunkBytes / 16));
+        const uint64_t b = b0 + (uint64_t)((tap * NKC + kc) * N * 2);
+        tc_mma_bf16(tmem + mt * N, a, b, idesc, (tap | kc) != 0);
       }
     }
   }
@@ -506,7 +513,7 @@ __global__ void __launch_bounds__(kNetThreads, 2)
     bool mine = true;
     if (tid == 0) {
       if (!weights_ready) mine = weights_ready = mbar_wait_bounded(wbar, 0, kNetWaitNs);
-      if (mine) issue_layer(sbase, kSmXA, kSmW, 32, 1, 0, kMT, tmem, bar);
+      if (mine) issue_layer<32, 1, 0, kMT>(sbase, kSmXA, kSmW, tmem, bar);
       else tc_commit(bar);
     }
     if (!(ok = wait_layer(bar, phase, mine))) break;
@@ -516,7 +523,7 @@ __global__ void __launch_bounds__(kNetThreads, 2)
     __syncthreads();
     tc_fence_after();
     // layer 2: 32 -> 32
-    if (tid == 0) issue_layer(sbase, kSmX1, kSmW + kW1Bytes, 32, 2, 0, kMT, tmem, bar);
+    if (tid == 0) issue_layer<32, 2, 0, kMT>(sbase, kSmX1, kSmW + kW1Bytes, tmem, bar);
     if (!(ok = wait_layer(bar, phase, true))) break;
     hidden_epilogue(tmem, bias + 32, sm + kSmXA);
     fence_proxy_async_smem();
@@ -524,7 +531,7 @@ __global__ void __launch_bounds__(kNetThreads, 2)
     __syncthreads();
     tc_fence_after();
     // layer 3: 32 -> 4 (N = 16), only the M tiles that hold the kept outputs
-    if (tid == 0) issue_layer(sbase, kSmXA, kSmW + kW1Bytes + kW2Bytes, 16, 2, kL3First, kL3Tiles, tmem, bar);
+    if (tid == 0) issue_layer<16, 2, kL3First, kL3Tiles>(sbase, kSmXA, kSmW + kW1Bytes + kW2Bytes, tmem, bar);
     if (!(ok = wait_layer(bar, phase, true))) break;
 #pragma unroll 1
     for (int mt = 0; mt < kL3Tiles && warp < 4; ++mt) {  // warps 0-3: one cell per lane
