@@ -94,6 +94,32 @@ def test_training_pair_and_features_match_oracle():
         np.testing.assert_allclose(an.cpu().numpy(), ar, rtol=1e-5, atol=1e-6 * np.max(np.abs(ar)))
 
 
+def test_tensor_core_forward_with_more_tiles_than_resident_ctas():
+    """2 x 13 x 19 = 494 ragged 16 x 16 tiles, more than the 2 x 152 CTAs the tensor-core kernel
+    keeps resident, so CTAs take several tiles in turn (the mbarrier phases and the TMEM
+    accumulators carry over from tile to tile); checked against the binary32 forward pass."""
+    import torch
+    theta = _params(11)
+    rng = np.random.default_rng(12)
+    x = torch.tensor(rng.normal(size=(2, 12, 200, 300)), dtype=torch.float32, device="cuda")
+    with lbmhd.Closure(theta, IN_SCALE, OUT_SCALE) as cl:
+        o32 = torch.empty((2, 4, 200, 300), dtype=torch.float32, device="cuda")
+        cl.forward(x, o32, tensor_cores=False)
+        o16 = torch.empty_like(o32)
+        cl.forward(x, o16, tensor_cores=True)
+        o16b = torch.empty_like(o32)
+        cl.forward(x, o16b, tensor_cores=True)
+    a, b = o32.cpu().numpy(), o16.cpu().numpy()
+    assert np.isfinite(b).all()
+    assert np.array_equal(b, o16b.cpu().numpy())  # deterministic
+    scale = np.sqrt(np.mean(a ** 2))
+    assert np.sqrt(np.mean((b - a) ** 2)) < 2e-2 * scale
+    # every tile is written: the worst tile's error is of the same order as the mean
+    err = np.abs(b - a).reshape(2, 4, 200, 300)
+    worst = max(err[:, :, y:y + 16, x0:x0 + 16].mean() for y in range(0, 200, 16) for x0 in range(0, 300, 16))
+    assert worst < 10 * err.mean() + 1e-3 * scale
+
+
 @pytest.mark.parametrize("precision,tol", [(lbmhd.LBMHD_FP64, 1e-13), (lbmhd.LBMHD_FP32, 2e-7)])
 def test_static_correction_matches_oracle(precision, tol):
     import torch
