@@ -220,6 +220,13 @@ int lbmhd_closure_train_step(lbmhd_closure_t* c, const float* x, const float* t,
  * LBMHD_ERR_TIMEOUT if a tensor-core completion wait of the fused kernel ran out (2 s). */
 int lbmhd_closure_forward(lbmhd_closure_t* c, const float* x, int batch, int h, int w, float* out,
                           int tensor_cores);
+/* Failure-detection test hook of the tensor-core forward pass.  With enable = 1, every
+ * following lbmhd_closure_forward(..., tensor_cores = 1) leaves out the first tile's layer-1
+ * MMAs and their commit in each CTA, so the time-bounded completion wait (2 s) runs out: the
+ * kernel stops without a GPU fault, frees its tensor memory and the call returns
+ * LBMHD_ERR_TIMEOUT (its output is then invalid).  enable = 0 restores normal calls; steps of
+ * handles the closure is attached to are not affected.  For tests of the error path only. */
+int lbmhd_closure_test_skip_mma(lbmhd_closure_t* c, int enable);
 const char* lbmhd_closure_last_error(const lbmhd_closure_t* c);
 void lbmhd_closure_free(lbmhd_closure_t* c);
 /* Attach a closure to a square binary64 / binary32 handle (NULL detaches): every step then runs

@@ -449,7 +449,7 @@ template <int SRC>
 __global__ void __launch_bounds__(kNetThreads, 2)
     net_tc_kernel(const void* __restrict__ src, StepGeom g, const float* __restrict__ in_scale,
                   const unsigned char* __restrict__ packed, const float* __restrict__ oscale, int batch, int H,
-                  int W, float* __restrict__ out, unsigned* __restrict__ err) {
+                  int W, float* __restrict__ out, unsigned* __restrict__ err, int skip_mma) {
   extern __shared__ __align__(128) unsigned char net_smem_raw[];
   unsigned char* sm = net_smem_raw + ((128u - (smem_u32(net_smem_raw) & 127u)) & 127u);
   const uint32_t sbase = smem_u32(sm);
@@ -513,8 +513,10 @@ __global__ void __launch_bounds__(kNetThreads, 2)
     bool mine = true;
     if (tid == 0) {
       if (!weights_ready) mine = weights_ready = mbar_wait_bounded(wbar, 0, kNetWaitNs);
-      if (mine) issue_layer<32, 1, 0, kMT>(sbase, kSmXA, kSmW, tmem, bar);
-      else tc_commit(bar);
+      // test hook: with skip_mma the first tile's layer-1 MMAs and their commit are left out,
+      // so the completion wait below runs out (nothing is in flight when TMEM is freed)
+      if (mine && !(skip_mma && tile == blockIdx.x)) issue_layer<32, 1, 0, kMT>(sbase, kSmXA, kSmW, tmem, bar);
+      else if (!mine) tc_commit(bar);
     }
     if (!(ok = wait_layer(bar, phase, mine))) break;
     hidden_epilogue(tmem, bias, sm + kSmX1);
@@ -586,20 +588,20 @@ cudaError_t set_net_attributes() {
 template <int SRC>
 cudaError_t launch_net_impl(const void* src, const StepGeom& g, const float* in_scale, const unsigned char* packed,
                             const float* oscale, int batch, int H, int W, float* out, unsigned* err,
-                            cudaStream_t s) {
+                            int skip_mma, cudaStream_t s) {
   cudaError_t e = set_net_attributes<SRC>();
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   net_tc_kernel<SRC><<<net_grid(batch, H, W, sms), kNetThreads, kNetSmemBytes, s>>>(src, g, in_scale, packed, oscale,
-                                                                                    batch, H, W, out, err);
+                                                                                    batch, H, W, out, err, skip_mma);
   return cudaGetLastError();
 }
 
 cudaError_t launch_net(const float* in, const unsigned char* packed, const float* oscale, int batch, int H,
-                       int W, float* out, unsigned* err, cudaStream_t s) {
-  return launch_net_impl<0>(in, StepGeom{}, nullptr, packed, oscale, batch, H, W, out, err, s);
+                       int W, float* out, unsigned* err, int skip_mma, cudaStream_t s) {
+  return launch_net_impl<0>(in, StepGeom{}, nullptr, packed, oscale, batch, H, W, out, err, skip_mma, s);
 }
 
 // ---- features and training targets ----------------------------------------------------------
@@ -730,8 +732,8 @@ cudaError_t closure_correction(const lbmhd_closure_t* c, int precision, const vo
                                float* corr, unsigned* err, cudaStream_t s) {
   const float* sc = closure_device_scales(c);
   const unsigned char* pk = closure_device_packed(c);
-  if (precision == 0) return launch_net_impl<2>(pops, g, sc, pk, sc + 12, 1, g.ny, g.nx, corr, err, s);
-  return launch_net_impl<1>(pops, g, sc, pk, sc + 12, 1, g.ny, g.nx, corr, err, s);
+  if (precision == 0) return launch_net_impl<2>(pops, g, sc, pk, sc + 12, 1, g.ny, g.nx, corr, err, 0, s);
+  return launch_net_impl<1>(pops, g, sc, pk, sc + 12, 1, g.ny, g.nx, corr, err, 0, s);
 }
 
 }  // namespace lbmhd_gpu
@@ -747,6 +749,7 @@ struct lbmhd_closure {
   float* scales = nullptr;  // device: in_scale[12], out_scale[4]
   unsigned char* packed = nullptr;  // device: bf16 weights + fp32 biases for the tensor-core kernel
   unsigned* tc_err = nullptr;       // device: tensor-core wait timeout flag
+  int test_skip_mma = 0;            // failure-detection test hook (lbmhd_closure_test_skip_mma)
   float host_scales[16];
   int adam_t = 0;
   // training scratch (grown on demand)
@@ -962,7 +965,7 @@ int lbmhd_closure_forward(lbmhd_closure_t* c, const float* x, int batch, int h, 
   const float* p3 = c->params + kP1 + kP2;
   cudaStream_t s = c->stream;
   if (tensor_cores) {
-    CL_CUDA(c, launch_net(x, c->packed, nullptr, batch, h, w, out, c->tc_err, s));
+    CL_CUDA(c, launch_net(x, c->packed, nullptr, batch, h, w, out, c->tc_err, c->test_skip_mma, s));
   } else {
     const int g = grid_for((long)cells);
     conv_fwd_kernel<kC0, kC1, true><<<g, kThreads, 0, s>>>(x, p1, batch, h, w, c->a1);
@@ -1006,6 +1009,13 @@ int lbmhd_closure_features(lbmhd_closure_t* c, const double* state, int m, doubl
       state, m, 1, c->scales, c->scales + 12, delta * delta / 12.0, x, analytic, nullptr, nullptr);
   CL_CUDA(c, cudaGetLastError());
   CL_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBMHD_OK;
+}
+
+int lbmhd_closure_test_skip_mma(lbmhd_closure_t* c, int enable) {
+  if (!c) return cfail(nullptr, LBMHD_ERR_INVALID, "NULL argument");
+  CL_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->test_skip_mma = enable ? 1 : 0;
   return LBMHD_OK;
 }
 

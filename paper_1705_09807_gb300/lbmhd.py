@@ -130,6 +130,7 @@ def load_library(path: str | None = None):
             "lbmhd_closure_forward": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
             "lbmhd_closure_last_error": (ctypes.c_char_p, [_H]),
+            "lbmhd_closure_test_skip_mma": (ctypes.c_int, [_H, ctypes.c_int]),
             "lbmhd_closure_free": (None, [_H]),
             "lbmhd_step_count": (ctypes.c_int64, [_H]),
             "lbmhd_last_error": (ctypes.c_char_p, [_H]),
@@ -562,6 +563,9 @@ class Closure:
         b, _, hh, ww = x.shape
         self._check(load_library().lbmhd_closure_forward(
             self.h, _dptr32(x, x.numel()), b, hh, ww, _dptr32(out, out.numel()), int(tensor_cores)))
+
+    def test_skip_mma(self, enable: bool) -> None:
+        self._check(load_library().lbmhd_closure_test_skip_mma(self.h, 1 if enable else 0))
 
     def attach(self, h) -> None:
         _check(load_library().lbmhd_set_closure(h, self.h), h)

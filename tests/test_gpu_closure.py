@@ -120,6 +120,31 @@ def test_tensor_core_forward_with_more_tiles_than_resident_ctas():
     assert worst < 10 * err.mean() + 1e-3 * scale
 
 
+def test_tensor_core_wait_timeout_reported_and_closure_usable():
+    """Failure detection without a fault: the hook leaves out the first layer's MMAs, so the
+    kernel's time-bounded completion wait runs out; the call reports LBMHD_ERR_TIMEOUT, and
+    the next call (hook off) gives the normal result."""
+    import time
+    import torch
+    theta = _params(13)
+    rng = np.random.default_rng(14)
+    x = torch.tensor(rng.normal(size=(1, 12, 40, 40)), dtype=torch.float32, device="cuda")
+    with lbmhd.Closure(theta, IN_SCALE, OUT_SCALE) as cl:
+        ref = torch.empty((1, 4, 40, 40), dtype=torch.float32, device="cuda")
+        cl.forward(x, ref, tensor_cores=True)
+        cl.test_skip_mma(True)
+        out = torch.empty_like(ref)
+        t0 = time.perf_counter()
+        with pytest.raises(lbmhd.LbmhdError) as e:
+            cl.forward(x, out, tensor_cores=True)
+        assert e.value.code == lbmhd.LBMHD_ERR_TIMEOUT
+        assert time.perf_counter() - t0 > 1.5  # the wait limit, not an early exit
+        cl.test_skip_mma(False)
+        again = torch.empty_like(ref)
+        cl.forward(x, again, tensor_cores=True)
+        assert torch.equal(again, ref)
+
+
 @pytest.mark.parametrize("precision,tol", [(lbmhd.LBMHD_FP64, 1e-13), (lbmhd.LBMHD_FP32, 2e-7)])
 def test_static_correction_matches_oracle(precision, tol):
     import torch
