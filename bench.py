@@ -185,12 +185,13 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def make_sim(n, precision, delta, stream=None, nu=NU, delta_frac=1 / 32):
+def make_sim(n, precision, delta, stream=None, nu=NU, delta_frac=1 / 32, stencil=0):
     from paper_1705_09807_gb300 import lbmhd
     from paper_1705_09807_gb300.inputs import kh_jet
     prec = {"fp16": lbmhd.LBMHD_FP16, "fp32": lbmhd.LBMHD_FP32, "fp64": lbmhd.LBMHD_FP64}[precision]
     p = lbmhd.lbmhd_params_srt(n, n, nu, nu, delta, prec)
     p.cuda_stream = stream
+    p.grad_stencil = stencil
     fields = kh_jet(n, u0=0.05, delta_frac=delta_frac, b0=0.02, seed=1)
     return lbmhd.Lbmhd(p, *fields), fields
 
@@ -358,6 +359,8 @@ def side_measurements(n, a):
                                           peaks()[0], 4)}
     msl = rate(make_sim(n, "fp32", 2.0)[0], 2000)
     res["fp32_les_delta2"] = {"mlups": round(n * n / msl / 1e3, 2)}
+    msi = rate(make_sim(n, "fp32", 2.0, stencil=1)[0], 2000)
+    res["fp32_les_delta2_isotropic_stencil"] = {"mlups": round(n * n / msi / 1e3, 2)}
     # precision forms against the FP64 GPU run: 4096^2 KH jet, d = N/64, Delta = 2, with the
     # paper's constant-Re viscosity at 4096^2 (4e-3; the configuration's 2e-4 diverges before
     # step 1000 in this SRT model)
