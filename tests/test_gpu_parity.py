@@ -166,13 +166,15 @@ def test_fp32_short_runs_elementwise(nx, ny, stencil):
     assert np.max(np.abs(pops - ref)) < 2e-7
 
 
-def _sampled_full_size(n, precision, delta, nu, warm, tol, seed=1, delta_frac=1 / 32):
+def _sampled_full_size(n, precision, delta, nu, warm, tol, seed=1, delta_frac=1 / 32, stencil=0,
+                       mrt=False):
     """Full-size grid in the benchmark's launch configuration: after `warm` steps, one more GPU
     step must equal the oracle's single-cell collision of the GPU's own state at sampled cells
     (f_i(x + c_i) after the step = f*_i(x) from the state before it)."""
     fields = kh_jet(n, delta_frac=delta_frac, seed=seed)
-    s, sm = oracle.srt_rates(nu), oracle.rate_from_diffusivity(nu)
-    p = lbmhd.make_params(n, n, s, sm, delta, precision)
+    s = mrt_rates(nu) if mrt else oracle.srt_rates(nu)
+    sm = oracle.rate_from_diffusivity(nu)
+    p = lbmhd.make_params(n, n, s, sm, delta, precision, stencil)
     with lbmhd.Lbmhd(p, *fields) as sim:
         sim.step(warm)
         before = sim.populations()
@@ -184,7 +186,7 @@ def _sampled_full_size(n, precision, delta, nu, warm, tol, seed=1, delta_frac=1 
     pts += [tuple(int(v) for v in rng.integers(0, n, 2)) for _ in range(120)]
     worst = 0.0
     for (x, y) in pts:
-        fs, gs = oracle.collide_cell(f, g, s, sm, delta, x, y)
+        fs, gs = oracle.collide_cell(f, g, s, sm, delta, x, y, stencil=stencil)
         for i in range(9):
             xd, yd = (x + CX[i]) % n, (y + CY[i]) % n
             worst = max(worst, abs(after[i, yd, xd] - fs[i]), abs(after[9 + i, yd, xd] - gs[0, i]),
@@ -221,3 +223,9 @@ def test_full_size_2048_fp64_les_sampled():
                                                 (lbmhd.LBMHD_FP16, 30, 1e-4)])
 def test_full_size_4096_precision_config_sampled(precision, warm, tol):
     _sampled_full_size(4096, precision, 2.0, 2e-4, warm, tol, seed=3, delta_frac=1 / 64)
+
+
+@pytest.mark.slow
+def test_full_size_2048_fp32_les_mrt_isotropic_sampled():
+    # unequal MRT rates and the isotropic stencil in the benchmark's launch configuration
+    _sampled_full_size(2048, lbmhd.LBMHD_FP32, 2.0, 2e-3, 50, 1e-7, seed=4, stencil=1, mrt=True)
