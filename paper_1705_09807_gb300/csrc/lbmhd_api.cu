@@ -125,15 +125,15 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 3-D map {pitch, ny, 27} over one population copy, boxes of {box_width, 1, 9} (one row of one
-// 9-plane group: the strip plus box_lead columns on each side).
+// 3-D map {columns, 27 planes, ny rows} over one population copy, boxes of {box_width, 9, 1}
+// (one row of one 9-plane group: the strip plus box_lead columns on each side).
 int make_tensor_map(lbmhd_t* h, void* base, CUtensorMap* map) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return fail(nullptr, LBMHD_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   const cuuint64_t e = h->elem;
-  cuuint64_t dims[3] = {(cuuint64_t)h->geom.pitch, (cuuint64_t)h->geom.ny, (cuuint64_t)kQ};
-  cuuint64_t strides[2] = {(cuuint64_t)h->geom.pitch * e, (cuuint64_t)h->geom.plane * e};
-  cuuint32_t box[3] = {(cuuint32_t)box_width((int)e), 1, 9};
+  cuuint64_t dims[3] = {(cuuint64_t)h->geom.plane, (cuuint64_t)kQ, (cuuint64_t)h->geom.ny};
+  cuuint64_t strides[2] = {(cuuint64_t)h->geom.plane * e, (cuuint64_t)h->geom.pitch * e};
+  cuuint32_t box[3] = {(cuuint32_t)box_width((int)e), 9, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   const CUtensorMapDataType dt = e == 8   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                  : e == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -175,8 +175,8 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
   StepGeom& g = h->geom;
   g.nx = p->nx;
   g.ny = p->ny;
-  g.pitch = (p->nx + kXOff + 2 + 31) / 32 * 32;
-  g.plane = (size_t)g.pitch * p->ny;
+  g.plane = (p->nx + kXOff + 2 + 31) / 32 * 32;  // one row of one plane
+  g.pitch = (int)(kQ * g.plane);                  // one row of all 27 planes
   g.band = step_band_rows(p->nx, p->ny, p->precision, sms);
   // rates scaled by the diagonal of T T^T = (9, 6, 6, 4, 4, 12, 12, 180, 20) (Eq. FluidTMatrix)
   const double norm[9] = {9, 6, 6, 4, 4, 12, 12, 180, 20};
@@ -185,7 +185,7 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
   const double kd = p->delta * p->delta / 12.0;
   // undivided differences: central a(+1)-a(-1) = 2 d; isotropic 12 d
   h->coef.kq = p->grad_stencil == LBMHD_GRAD_ISOTROPIC ? kd / 144.0 : kd / 4.0;
-  h->state_bytes = (size_t)kQ * g.plane * h->elem;
+  h->state_bytes = (size_t)g.pitch * p->ny * h->elem;
   const size_t ncell = (size_t)p->nx * p->ny;
 #define LB_INIT(call)                 \
   do {                                \

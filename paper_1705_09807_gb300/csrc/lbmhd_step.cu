@@ -383,9 +383,9 @@ __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict_
     const int rc = r == ny - 1 ? 0 : r + 1;  // c_y = -1 group from row r + 1
     const int cx = x0 + kXOff - LEAD;        // box covers logical columns x0-LEAD .. x0+BW-LEAD-1
     mbar_arrive_expect_tx(&S_.full[s], SM::kTxBytes);
-    tma_load_3d(&S_.stage[s][0], srcp, cx, ra, 0, &S_.full[s]);
-    tma_load_3d(&S_.stage[s][GE], srcp, cx, r, 9, &S_.full[s]);
-    tma_load_3d(&S_.stage[s][2 * GE], srcp, cx, rc, 18, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][0], srcp, cx, 0, ra, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][GE], srcp, cx, 9, r, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][2 * GE], srcp, cx, 18, rc, &S_.full[s]);
   };
   auto slot = [&](int k) -> int { return (int)((kb + (uint32_t)k) % NST); };
   auto wait_row = [&](int k) -> bool {
@@ -601,9 +601,9 @@ __device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* _
     const int rc = r == ny - 1 ? 0 : r + 1;
     const int cx = x0 + kXOff - LEAD;
     mbar_arrive_expect_tx(&S_.full[s], SM::kTxBytes);
-    tma_load_3d(&S_.stage[s][0], srcp, cx, ra, 0, &S_.full[s]);
-    tma_load_3d(&S_.stage[s][GE], srcp, cx, r, 9, &S_.full[s]);
-    tma_load_3d(&S_.stage[s][2 * GE], srcp, cx, rc, 18, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][0], srcp, cx, 0, ra, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][GE], srcp, cx, 9, r, &S_.full[s]);
+    tma_load_3d(&S_.stage[s][2 * GE], srcp, cx, 18, rc, &S_.full[s]);
   };
   auto slot = [&](int k) -> int { return (int)((kb + (uint32_t)k) % NST); };
   auto wait_row = [&](int k) -> bool {
