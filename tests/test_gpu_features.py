@@ -196,3 +196,25 @@ def test_pipeline_wait_timeout_reported_and_context_usable(precision):
         sim.step(1)
         sim.moments()  # status clear again
         assert np.array_equal(sim.populations(), want)
+
+
+@pytest.mark.slow
+def test_grid_beyond_2_31_population_elements_matches_its_tile():
+    """Maximum-size indexing: a 16384 x 8192 binary32 grid holds 3.6e9 population elements per
+    copy (beyond 2^31).  Fields periodic with period 4096 in x evolve exactly as the 4096 x 8192
+    run tiled four times: every cell's arithmetic is the same, so any index error shows up."""
+    nx, ny, rep = 16384, 8192, 4
+    base = smooth_random_fields(nx // rep, ny, seed=21, amp_u=0.04, amp_b=0.03, amp_rho=0.01)
+    p_small = _params(1, lbmhd.LBMHD_FP32)
+    p_small.nx, p_small.ny = nx // rep, ny
+    with lbmhd.Lbmhd(p_small, *base) as small:
+        small.step(6)
+        ref = small.moments()
+    p_big = _params(1, lbmhd.LBMHD_FP32)
+    p_big.nx, p_big.ny = nx, ny
+    with lbmhd.Lbmhd(p_big, *(np.tile(a, (1, rep)) for a in base)) as big:
+        assert lbmhd.lbmhd_state_bytes(big.h) > 2 ** 31 * 4
+        big.step(6)
+        got = big.moments()
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, np.tile(b, (1, rep)))
