@@ -36,8 +36,8 @@ def common_flags(extra=()) -> list:
             "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra]
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, extra, build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj, *common_flags(extra)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -57,29 +57,47 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in deps)
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    if not force and not verbose_ptxas and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+def _build(lib: str, build_dir: str, extra) -> str:
+    os.makedirs(build_dir, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, extra, build_dir), SOURCES))
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc(), "-shared", "-o", tmp, *objs, *ARCH, "-cudart", "static", "-lrt", "-ldl",
            "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(force: bool = False, verbose_ptxas: bool = False) -> str:
+    if not force and not verbose_ptxas and up_to_date():
+        return LIB
+    return _build(LIB, BUILD, ["-Xptxas", "-v"] if verbose_ptxas else [])
+
+
+CHECK_LIB = os.path.join(PKG, "liblbmhd_check.so")
+
+
+def build_checked(force: bool = False) -> str:
+    """The bounds-checking variant of the library (-DLBMHD_BOUNDS_CHECK), beside the normal one:
+    the step kernels check their shared-memory, global-memory and copy indices, skip any access
+    that fails and set a flag that the next synchronising call reports as an error.  For tests;
+    the normal build compiles the checks away."""
+    if not force and os.path.exists(CHECK_LIB) and all(
+            os.path.getmtime(os.path.join(CSRC, f)) <= os.path.getmtime(CHECK_LIB) for f in os.listdir(CSRC)):
+        return CHECK_LIB
+    return _build(CHECK_LIB, os.path.join(PKG, "_build_check"), ["-DLBMHD_BOUNDS_CHECK"])
 
 
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--verbose-ptxas", action="store_true")
     ap.add_argument("--force", action="store_true")
+    ap.add_argument("--bounds-check", action="store_true", help="build the bounds-checking variant")
     a = ap.parse_args()
-    print(build(force=a.force, verbose_ptxas=a.verbose_ptxas))
+    print(build_checked(force=a.force) if a.bounds_check else build(force=a.force, verbose_ptxas=a.verbose_ptxas))
 
 
 if __name__ == "__main__":

@@ -152,6 +152,10 @@ int check_step_status(lbmhd_t* h) {
   unsigned v = 0;
   LB_CUDA(h, cudaMemcpy(&v, h->err_flag, sizeof v, cudaMemcpyDeviceToHost));
   if (v) return fail(h, LBMHD_ERR_TIMEOUT, "a fused-step pipeline wait timed out; the state is invalid");
+#ifdef LBMHD_BOUNDS_CHECK
+  if (const unsigned bf = bounds_check_flags())
+    return fail(h, LBMHD_ERR_INVALID, "bounds check failed in a step kernel (flags 0x%x)", bf);
+#endif
   return LBMHD_OK;
 }
 

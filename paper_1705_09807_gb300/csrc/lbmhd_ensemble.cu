@@ -366,6 +366,10 @@ int lbmhd_ensemble_sync(lbmhd_ensemble_t* e) {
   unsigned errv = 0;
   ENS_CUDA(e, cudaMemcpy(&errv, e->d_err, sizeof errv, cudaMemcpyDeviceToHost));
   if (errv) return efail(e, LBMHD_ERR_TIMEOUT, "a pipeline wait timed out; the states are invalid");
+#ifdef LBMHD_BOUNDS_CHECK
+  if (const unsigned bf = bounds_check_flags())
+    return efail(e, LBMHD_ERR_INVALID, "bounds check failed in a step kernel (flags 0x%x)", bf);
+#endif
   return LBMHD_OK;
 }
 

@@ -115,6 +115,10 @@ cudaError_t launch_step_f16(const CUtensorMap& src, __half* dst, const StepGeom&
 int step_band_rows(int nx, int ny, int precision, int num_sms);
 // Opt the step kernels in to their dynamic shared memory (once per process and device).
 cudaError_t prepare_step_kernels();
+#ifdef LBMHD_BOUNDS_CHECK
+// Bounds-checking build: the step kernels' failed-check bits since the last call (cleared).
+unsigned bounds_check_flags();
+#endif
 
 // Ensemble step (lbmhd_step.cu): the member table is packed on the host into
 // ensemble_member_bytes(precision) * n bytes and copied to the device; work[i] = {member,

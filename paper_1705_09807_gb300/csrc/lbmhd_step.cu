@@ -34,6 +34,7 @@
 //   J_a J_b / rho -> (J_a J_b + k G_ab)/rho,  B_a B_b -> B_a B_b + k H_ab,
 //   E -> (J_x B_y - J_y B_x + k (K_xy - K_yx))/rho,   k = Delta^2/12,
 //   G_ab = d_b'J_a d_b'J_b, H_ab = d_b'B_a d_b'B_b, K_ab = d_b'J_a d_b'B_b (sum over b').
+#include <cstdlib>
 #include <mutex>
 
 #include "lbmhd_internal.cuh"
@@ -43,6 +44,21 @@ namespace lbmhd_gpu {
 namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per mbarrier wait
+
+// Index checks of the bounds-checking build (-DLBMHD_BOUNDS_CHECK, a stand-in for a memory
+// checker): LB_IN(cond, bit) is true in the normal build; in the checking build a false cond sets
+// `bit` in g_bounds_flags (0: staged-row column, 1: moment-ring extent, 2: global store, 3: copy
+// coordinates) and the caller skips the access.  The bits of g_bounds_force (environment
+// variable LBMHD_BOUNDS_FORCE, read when the kernels are prepared) fail their checks whatever
+// cond says, so that a test can see the skip-and-report path work.
+#ifdef LBMHD_BOUNDS_CHECK
+__device__ unsigned g_bounds_flags;
+__device__ unsigned g_bounds_force;
+#define LB_IN(cond, bit) \
+  (((cond) && !((g_bounds_force >> (bit)) & 1u)) || (atomicOr(&g_bounds_flags, 1u << (bit)), false))
+#else
+#define LB_IN(cond, bit) true
+#endif
 
 template <typename T>
 struct KCoef {
@@ -298,11 +314,11 @@ struct StepSmem {
 // Store the 27 post-collision values of one cell, planes in address order through one advancing
 // pointer (fewer address instructions than 27 independent 64-bit plane offsets).
 template <typename S, typename T, int PL>
-__device__ __forceinline__ void store_planes(S* op, const T* p, size_t plane) {
+__device__ __forceinline__ void store_planes(S* op, const T* p, size_t plane, const S* lo, const S* hi) {
   if constexpr (PL < kQ) {
     constexpr int q = q_of_plane(PL);
-    *op = store_as<S>(p[q]);
-    store_planes<S, T, PL + 1>(op + plane, p, plane);
+    if (LB_IN(op >= lo && op < hi, 2)) *op = store_as<S>(p[q]);
+    store_planes<S, T, PL + 1>(op + plane, p, plane, lo, hi);
   }
 }
 
@@ -310,7 +326,9 @@ __device__ __forceinline__ void store_planes(S* op, const T* p, size_t plane) {
 template <typename C, typename S, int BW>
 __device__ __forceinline__ C staged(const S* st, int ge, int q, int col) {
   const int i = q % 9;
-  return load_as<C>(st[group_of(i) * ge + (3 * (q / 9) + index_in_group(i)) * BW + col - vel_x(i)]);
+  const int c = col - vel_x(i);
+  if (!LB_IN(c >= 0 && c < BW, 0)) return C(0);
+  return load_as<C>(st[group_of(i) * ge + (3 * (q / 9) + index_in_group(i)) * BW + c]);
 }
 
 template <typename C, typename S, int BW>
@@ -363,6 +381,8 @@ __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict_
   const int nx = g.nx, ny = g.ny;
   const int ncol = min(kStepThreads, nx - x0);
   const bool active = t < ncol;
+  // the ring holds columns -1 .. ncol at indices 0 .. ncol + 1 (uniform over the block)
+  if (!LB_IN(ncol >= 1 && ncol + 1 < SM::kRingW, 1)) return true;
   const int y1 = min(y0 + g.band, ny);
   const int L = (y1 - y0) + 2;  // rows staged: the band and one on each side
   const int dir = (band_parity & 1) ? -1 : 1;
@@ -382,10 +402,13 @@ __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict_
     const int ra = r == 0 ? ny - 1 : r - 1;  // c_y = +1 group is pulled from row r - 1
     const int rc = r == ny - 1 ? 0 : r + 1;  // c_y = -1 group from row r + 1
     const int cx = x0 + kXOff - LEAD;        // box covers logical columns x0-LEAD .. x0+BW-LEAD-1
-    mbar_arrive_expect_tx(&S_.full[s], SM::kTxBytes);
-    tma_load_3d(&S_.stage[s][0], srcp, cx, 0, ra, &S_.full[s]);
-    tma_load_3d(&S_.stage[s][GE], srcp, cx, 9, r, &S_.full[s]);
-    tma_load_3d(&S_.stage[s][2 * GE], srcp, cx, 18, rc, &S_.full[s]);
+    const bool in = LB_IN(ra >= 0 && ra < ny && r >= 0 && r < ny && rc >= 0 && rc < ny && cx >= 0, 3);
+    mbar_arrive_expect_tx(&S_.full[s], in ? SM::kTxBytes : 0u);  // 0: the phase completes empty
+    if (in) {
+      tma_load_3d(&S_.stage[s][0], srcp, cx, 0, ra, &S_.full[s]);
+      tma_load_3d(&S_.stage[s][GE], srcp, cx, 9, r, &S_.full[s]);
+      tma_load_3d(&S_.stage[s][2 * GE], srcp, cx, 18, rc, &S_.full[s]);
+    }
   };
   auto slot = [&](int k) -> int { return (int)((kb + (uint32_t)k) % NST); };
   auto wait_row = [&](int k) -> bool {
@@ -506,14 +529,21 @@ __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict_
         collide(p, rho_cur, jx, jy, bx, by, dJ, dB, c);
       }
       S* o = dst + (size_t)y * pitch + kXOff + x;
-      store_planes<S, T, 0>(o, p, g.plane);
+      const S* end = dst + (size_t)g.pitch * ny;  // one past the copy (checking build)
+      store_planes<S, T, 0>(o, p, g.plane, dst, end);
       if (x < 2) {  // right ghosts: logical columns nx, nx + 1
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) o[(size_t)plane_of(q) * g.plane + nx] = store_as<S>(p[q]);
+        for (int q = 0; q < kQ; ++q) {
+          S* a = o + (size_t)plane_of(q) * g.plane + nx;
+          if (LB_IN(a >= dst && a < end, 2)) *a = store_as<S>(p[q]);
+        }
       }
       if (x >= nx - 2) {  // left ghosts: logical columns -2, -1
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) o[(size_t)plane_of(q) * g.plane - nx] = store_as<S>(p[q]);
+        for (int q = 0; q < kQ; ++q) {
+          S* a = o + (size_t)plane_of(q) * g.plane - nx;
+          if (LB_IN(a >= dst && a < end, 2)) *a = store_as<S>(p[q]);
+        }
       }
     }
     rho_cur = rho_next;
@@ -526,7 +556,9 @@ __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict_
 template <int BW>
 __device__ __forceinline__ F2 staged_pair(const __half* st, int ge, int q, int col) {
   const int i = q % 9;
-  const __half* a = st + group_of(i) * ge + (3 * (q / 9) + index_in_group(i)) * BW + col - vel_x(i);
+  const int c = col - vel_x(i);
+  if (!LB_IN(c >= 0 && c + 1 < BW && (vel_x(i) != 0 || c % 2 == 0), 0)) return f2(0.f);
+  const __half* a = st + group_of(i) * ge + (3 * (q / 9) + index_in_group(i)) * BW + c;
   if (vel_x(i) == 0) {  // even column: one aligned 32-bit load
     const float2 v = __half22float2(*reinterpret_cast<const __half2*>(a));
     return f2(v.x, v.y);
@@ -549,14 +581,17 @@ __device__ __forceinline__ void moments_pair(const __half* st, int ge, int col, 
 // Store the 27 values of two adjacent cells (binary16 pairs, one 32-bit store per plane), planes
 // in address order; `both` false stores the first cell only (odd strip width).
 template <int PL>
-__device__ __forceinline__ void store_planes_pair(__half* op, const F2* p, size_t plane, bool both) {
+__device__ __forceinline__ void store_planes_pair(__half* op, const F2* p, size_t plane, bool both,
+                                                  const __half* lo_end, const __half* hi_end) {
   if constexpr (PL < kQ) {
     constexpr int q = q_of_plane(PL);
-    if (both)
-      *reinterpret_cast<__half2*>(op) = __floats2half2_rn(lo(p[q]), hi(p[q]));
-    else
-      *op = __float2half_rn(lo(p[q]));
-    store_planes_pair<PL + 1>(op + plane, p, plane, both);
+    if (LB_IN(op >= lo_end && op + (both ? 2 : 1) <= hi_end, 2)) {
+      if (both)
+        *reinterpret_cast<__half2*>(op) = __floats2half2_rn(lo(p[q]), hi(p[q]));
+      else
+        *op = __float2half_rn(lo(p[q]));
+    }
+    store_planes_pair<PL + 1>(op + plane, p, plane, both, lo_end, hi_end);
   }
 }
 
@@ -580,6 +615,8 @@ __device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* _
   const int nx = g.nx, ny = g.ny;
   const int ncol = min(kStepThreads, nx - x0);
   const bool active = c0 < ncol;
+  // ring indices 1 .. ncol + 3 are read or written (uniform over the block)
+  if (!LB_IN(ncol >= 1 && ncol + 3 < RW, 1)) return true;
   const int last = (ncol - 1) / 2;  // thread holding the strip's last column
   const int y1 = min(y0 + g.band, ny);
   const int L = (y1 - y0) + 2;
@@ -600,10 +637,13 @@ __device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* _
     const int ra = r == 0 ? ny - 1 : r - 1;
     const int rc = r == ny - 1 ? 0 : r + 1;
     const int cx = x0 + kXOff - LEAD;
-    mbar_arrive_expect_tx(&S_.full[s], SM::kTxBytes);
-    tma_load_3d(&S_.stage[s][0], srcp, cx, 0, ra, &S_.full[s]);
-    tma_load_3d(&S_.stage[s][GE], srcp, cx, 9, r, &S_.full[s]);
-    tma_load_3d(&S_.stage[s][2 * GE], srcp, cx, 18, rc, &S_.full[s]);
+    const bool in = LB_IN(ra >= 0 && ra < ny && r >= 0 && r < ny && rc >= 0 && rc < ny && cx >= 0, 3);
+    mbar_arrive_expect_tx(&S_.full[s], in ? SM::kTxBytes : 0u);  // 0: the phase completes empty
+    if (in) {
+      tma_load_3d(&S_.stage[s][0], srcp, cx, 0, ra, &S_.full[s]);
+      tma_load_3d(&S_.stage[s][GE], srcp, cx, 9, r, &S_.full[s]);
+      tma_load_3d(&S_.stage[s][2 * GE], srcp, cx, 18, rc, &S_.full[s]);
+    }
   };
   auto slot = [&](int k) -> int { return (int)((kb + (uint32_t)k) % NST); };
   auto wait_row = [&](int k) -> bool {
@@ -723,7 +763,8 @@ __device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* _
       const int y = row_of(m);
       const int x = x0 + c0;
       __half* o = dst + (size_t)y * pitch + kXOff + x;
-      store_planes_pair<0>(o, p, g.plane, c0 + 1 < ncol);
+      const __half* end = dst + (size_t)g.pitch * ny;  // one past the copy (checking build)
+      store_planes_pair<0>(o, p, g.plane, c0 + 1 < ncol, dst, end);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int xh = x + h;
@@ -731,7 +772,10 @@ __device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* _
         if (xh < 2 || xh >= nx - 2) {  // ghosts: logical nx, nx + 1 and -2, -1
           __half* gp = o + h + (xh < 2 ? nx : -nx);
 #pragma unroll
-          for (int q = 0; q < kQ; ++q) gp[(size_t)plane_of(q) * g.plane] = __float2half_rn(h ? hi(p[q]) : lo(p[q]));
+          for (int q = 0; q < kQ; ++q) {
+            __half* a = gp + (size_t)plane_of(q) * g.plane;
+            if (LB_IN(a >= dst && a < end, 2)) *a = __float2half_rn(h ? hi(p[q]) : lo(p[q]));
+          }
         }
       }
     }
@@ -957,10 +1001,24 @@ cudaError_t launch_ens(int stencil, const void* members, const int4* work, int n
 
 }  // namespace
 
+#ifdef LBMHD_BOUNDS_CHECK
+unsigned bounds_check_flags() {
+  unsigned v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_bounds_flags, sizeof v) != cudaSuccess) return ~0u;
+  cudaMemcpyToSymbol(g_bounds_flags, &z, sizeof z);
+  return v;
+}
+#endif
+
 cudaError_t prepare_step_kernels() {
   cudaError_t e = set_smem_attr<float>();
   if (e == cudaSuccess) e = set_smem_attr<double>();
   if (e == cudaSuccess) e = set_smem_attr<__half>();
+#ifdef LBMHD_BOUNDS_CHECK
+  const char* env = getenv("LBMHD_BOUNDS_FORCE");
+  const unsigned force = env ? (unsigned)strtoul(env, nullptr, 0) : 0u;
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bounds_force, &force, sizeof force);
+#endif
   return e;
 }
 

@@ -103,3 +103,11 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(lbmhd, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         lbmhd.load_library(str(tmp_path / "nope.so"))
+
+
+@pytest.mark.slow
+def test_bounds_checking_variant_builds_and_exports_the_same_functions():
+    path = libbuild.build_checked()
+    chk = ctypes.CDLL(path)
+    for n in lbmhd.header_functions():
+        assert hasattr(chk, n), n
