@@ -811,6 +811,7 @@ __global__ void __launch_bounds__(step_threads<S>(), MINB)
                       const float* __restrict__ corr) {
   if ((int)blockIdx.y * g.band >= g.ny) return;  // uniform per block
   init_stage_barriers(step_smem<S, NST>(), &src);
+  grid_dependency_wait();  // the previous step has written src (and read dst)
   uint32_t kbase = 0;
   run_any_tile<S, ISO, NST, CORR>(&src, dst, g, c, blockIdx.x * kStepThreads, blockIdx.y * g.band, blockIdx.y,
                                   kbase, err, corr);
@@ -833,6 +834,7 @@ __global__ void __launch_bounds__(step_threads<S>(), MINB)
                          int nwork, int parity, unsigned long long* queue, unsigned* __restrict__ err) {
   __shared__ int next_item;
   init_stage_barriers(step_smem<S, NST>(), nullptr);
+  grid_dependency_wait();
   uint32_t kbase = 0;
   int w = blockIdx.x;
   if (queue) {
@@ -929,25 +931,44 @@ constexpr size_t smem_bytes() {
   return sizeof(StepSmem<S, StepConfig<S>::kStages>) + 128;  // + alignment slack
 }
 
+// Launch with programmatic stream serialisation: the blocks of a step may be scheduled while the
+// previous kernel in the stream drains; each waits (grid_dependency_wait) before touching global
+// memory.  Measured: 6.5% less time per step at 256^2 binary32, 10% at 128^2, 3% at 512^2,
+// large grids unchanged (bitwise the same results); letting dependants launch early
+// (griddepcontrol.launch_dependents at block start) instead of at block exit made small grids
+// slower (128^2 binary32 23% slower).
+template <typename K, typename... A>
+cudaError_t launch_programmatic(K kernel, dim3 grid, int threads, size_t smem, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename S>
 cudaError_t launch_step(const CUtensorMap& src, S* dst, const StepGeom& g, const StepCoef& c,
                         int stencil, unsigned* err, const float* corr, cudaStream_t s) {
   dim3 grid((g.nx + kStepThreads - 1) / kStepThreads, (g.ny + g.band - 1) / g.band);
   auto k = cast_coef<typename ArithOf<S>::type>(c);
+  const int nt = step_threads<S>();
+  const size_t sm = smem_bytes<S>();
   if (corr) {
-    if constexpr (sizeof(S) == 2) {
+    if constexpr (sizeof(S) == 2)
       return cudaErrorNotSupported;  // the correction is offered for binary64 / binary32 storage
-    } else if (stencil == 1) {
-      kernel_ptr<S, 1, true>()<<<grid, step_threads<S>(), smem_bytes<S>(), s>>>(src, dst, g, k, err, corr);
-    } else {
-      kernel_ptr<S, 0, true>()<<<grid, step_threads<S>(), smem_bytes<S>(), s>>>(src, dst, g, k, err, corr);
-    }
-  } else if (stencil == 1) {
-    kernel_ptr<S, 1>()<<<grid, step_threads<S>(), smem_bytes<S>(), s>>>(src, dst, g, k, err, nullptr);
-  } else {
-    kernel_ptr<S, 0>()<<<grid, step_threads<S>(), smem_bytes<S>(), s>>>(src, dst, g, k, err, nullptr);
+    else
+      return stencil == 1 ? launch_programmatic(kernel_ptr<S, 1, true>(), grid, nt, sm, s, src, dst, g, k, err, corr)
+                          : launch_programmatic(kernel_ptr<S, 0, true>(), grid, nt, sm, s, src, dst, g, k, err, corr);
   }
-  return cudaGetLastError();
+  const float* none = nullptr;
+  return stencil == 1 ? launch_programmatic(kernel_ptr<S, 1>(), grid, nt, sm, s, src, dst, g, k, err, none)
+                      : launch_programmatic(kernel_ptr<S, 0>(), grid, nt, sm, s, src, dst, g, k, err, none);
 }
 
 template <typename S, int ISO>
@@ -992,6 +1013,13 @@ template <typename S>
 cudaError_t launch_ens(int stencil, const void* members, const int4* work, int nwork, int parity,
                        unsigned long long* queue, int grid, unsigned* err, cudaStream_t s) {
   const EnsembleMember<S>* mb = static_cast<const EnsembleMember<S>*>(members);
+  if (!queue)  // static schedule: the previous launch is the previous step kernel
+    return stencil == 1
+               ? launch_programmatic(ensemble_kernel_ptr<S, 1>(), dim3(grid), step_threads<S>(), smem_bytes<S>(), s,
+                                     mb, work, nwork, parity, queue, err)
+               : launch_programmatic(ensemble_kernel_ptr<S, 0>(), dim3(grid), step_threads<S>(), smem_bytes<S>(), s,
+                                     mb, work, nwork, parity, queue, err);
+  // persistent schedule: a memset of the tile counter precedes each launch; ordinary ordering
   if (stencil == 1)
     ensemble_kernel_ptr<S, 1>()<<<grid, step_threads<S>(), smem_bytes<S>(), s>>>(mb, work, nwork, parity, queue, err);
   else

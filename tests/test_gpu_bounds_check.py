@@ -135,3 +135,46 @@ def test_forced_check_failures_are_skipped_and_reported():
         assert f" {lbmhd.LBMHD_ERR_INVALID} " in ln and "flags 0xd" in ln, ln
     unchanged = [ln for ln in out if ln.startswith("UNCHANGED")]
     assert len(unchanged) == 3 and all(ln.endswith("True") for ln in unchanged), r.stdout
+
+
+FULL = textwrap.dedent('''
+    import sys
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1705_09807_gb300 import lbmhd
+    from paper_1705_09807_gb300.inputs import kh_jet
+    lbmhd.load_library(LIB)
+    # the benchmark's launch configurations: 2048^2 (54-row binary32 bands, one wave of
+    # blocks) and 4096^2, every storage form
+    for n, prec, delta, steps in ((2048, lbmhd.LBMHD_FP32, 0.0, 34), (2048, lbmhd.LBMHD_FP16, 2.0, 34),
+                                  (2048, lbmhd.LBMHD_FP64, 2.0, 3), (4096, lbmhd.LBMHD_FP32, 2.0, 3),
+                                  (4096, lbmhd.LBMHD_FP16, 0.0, 3)):
+        p = lbmhd.lbmhd_params_srt(n, n, 5e-4, 5e-4, delta, prec)
+        with lbmhd.Lbmhd(p, *kh_jet(n, seed=1)) as sim:
+            sim.step(steps)
+            rho = sim.moments()[0]
+            assert np.all(np.isfinite(rho)) and abs(rho.mean() - 1) < 1e-3
+        print("CLEAN", n, prec)
+    # the 48-run ensemble (16 each of 128^2, 512^2, 1024^2), both schedules
+    mem = []
+    for i, n in enumerate([128] * 16 + [512] * 16 + [1024] * 16):
+        p = lbmhd.lbmhd_params_srt(n, n, 2e-3, 2e-3, 2.0, lbmhd.LBMHD_FP32)
+        mem.append((p, kh_jet(n, seed=100 + i)))
+    with lbmhd.Ensemble(mem) as ens:
+        for rows, persistent in ((0, False), (8, True)):
+            ens.set_schedule(rows, persistent)
+            ens.step(3)
+            ens.sync()
+    print("CLEAN ensemble")
+''')
+
+
+@pytest.mark.slow
+def test_bounds_checked_build_at_the_benchmark_sizes():
+    from paper_1705_09807_gb300 import build
+    lib = build.build_checked()
+    code = f"ROOT = {ROOT!r}\nLIB = {lib!r}\n" + FULL
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    assert r.stdout.count("CLEAN") == 6, r.stdout
