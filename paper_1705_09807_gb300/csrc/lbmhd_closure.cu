@@ -464,7 +464,16 @@ __global__ void __launch_bounds__(kNetThreads, 2)
     mbar_init(bar, 1);
     mbar_init(wbar, 1);
     fence_barrier_init();
-    // the weights (bf16, already in the operand layout) arrive by one bulk copy
+  }
+  // zero pad cells of the 8 activation chunks (shifted reads reach kPS + 1 cells beyond 0 .. 511)
+  for (int i = tid; i < 8 * 2 * kPadCells; i += kNetThreads) {
+    const int ch = i / (2 * kPadCells), j = i % (2 * kPadCells);
+    const int cell = j < kPadCells ? j : kMT * 128 + j;
+    *reinterpret_cast<uint4*>(sm + kSmXA + ch * kChunkBytes + cell * 16) = make_uint4(0, 0, 0, 0);
+  }
+  // global reads start here: with a programmatic launch the previous step may still be draining
+  grid_dependency_wait();
+  if (tid == 0) {
     mbar_arrive_expect_tx(wbar, kWBytes);
     bulk_copy_g2s(sm + kSmW, packed, kWBytes, wbar);
   }
@@ -474,12 +483,6 @@ __global__ void __launch_bounds__(kNetThreads, 2)
     else if (i < kBiasFloats + 4) v = oscale ? oscale[i - kBiasFloats] : 1.f;
     else v = SRC ? 1.f / in_scale[i - kBiasFloats - 4] : 1.f;
     bias[i] = v;
-  }
-  // zero pad cells of the 8 activation chunks (shifted reads reach kPS + 1 cells beyond 0 .. 511)
-  for (int i = tid; i < 8 * 2 * kPadCells; i += kNetThreads) {
-    const int ch = i / (2 * kPadCells), j = i % (2 * kPadCells);
-    const int cell = j < kPadCells ? j : kMT * 128 + j;
-    *reinterpret_cast<uint4*>(sm + kSmXA + ch * kChunkBytes + cell * 16) = make_uint4(0, 0, 0, 0);
   }
   if (warp == 0) {
     tmem_alloc(slot, kTmemCols);
@@ -594,9 +597,8 @@ cudaError_t launch_net_impl(const void* src, const StepGeom& g, const float* in_
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  net_tc_kernel<SRC><<<net_grid(batch, H, W, sms), kNetThreads, kNetSmemBytes, s>>>(src, g, in_scale, packed, oscale,
-                                                                                    batch, H, W, out, err, skip_mma);
-  return cudaGetLastError();
+  return launch_programmatic(net_tc_kernel<SRC>, dim3(net_grid(batch, H, W, sms)), kNetThreads, (size_t)kNetSmemBytes,
+                             s, src, g, in_scale, packed, oscale, batch, H, W, out, err, skip_mma);
 }
 
 cudaError_t launch_net(const float* in, const unsigned char* packed, const float* oscale, int batch, int H,

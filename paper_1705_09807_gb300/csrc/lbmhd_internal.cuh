@@ -174,4 +174,23 @@ cudaStream_t closure_stream(const lbmhd_closure_t* c);
 // Store a message for lbmhd_last_error(NULL) on the calling thread (lbmhd_api.cu).
 void set_thread_error(const char* msg);
 
+// Launch `kernel` with programmatic stream serialisation: its blocks may be scheduled while the
+// previous kernel in the stream drains (dependants are released at that kernel's block exit);
+// the kernel must wait (griddepcontrol.wait) before its first global-memory access.  After a
+// copy or a memset the launch is ordered as usual.
+template <typename K, typename... A>
+cudaError_t launch_programmatic(K kernel, dim3 grid, int threads, size_t smem, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace lbmhd_gpu

@@ -360,6 +360,29 @@ __device__ __forceinline__ void init_stage_barriers(StepSmem<S, NST>& S_, const 
   }
 }
 
+// The three boxes of staged row r (groups c_y = +1, 0, -1 from rows ra, r, rc) into one stage.
+// The first two rows a band stages are also the first two of the neighbouring band that marches
+// the other way: `keep` asks L2 to keep their lines (evict_last) for that second reader.
+// Measured: 2048^2 binary32 1.6% and binary16 0.8% less time per step (DRAM reads of a warm
+// binary32 step 1% lower), 4096^2, binary64 and 256^2 unchanged; the same hint on the last two
+// rows instead helped less (binary32 1.0%, binary16 none), and streaming (evict_first) the
+// other rows made every form slower (binary32 15% more time, DRAM reads 470 -> 518 MB per step:
+// neighbouring strips then re-read their overlapping box columns from DRAM).
+template <typename S>
+__device__ __forceinline__ void copy_row_boxes(S* stage, int ge, const CUtensorMap* srcp, int cx, int ra, int r, int rc,
+                                               uint64_t* bar, bool keep) {
+  if (keep) {
+    const uint64_t pol = l2_policy_evict_last();
+    tma_load_3d_hint(stage, srcp, cx, 0, ra, bar, pol);
+    tma_load_3d_hint(stage + ge, srcp, cx, 9, r, bar, pol);
+    tma_load_3d_hint(stage + 2 * ge, srcp, cx, 18, rc, bar, pol);
+  } else {
+    tma_load_3d(stage, srcp, cx, 0, ra, bar);
+    tma_load_3d(stage + ge, srcp, cx, 9, r, bar);
+    tma_load_3d(stage + 2 * ge, srcp, cx, 18, rc, bar);
+  }
+}
+
 // One tile: the strip of kStepThreads columns starting at x0 and the band of rows [y0, y0 + band)
 // of one grid, marched in direction +1 (band_parity even) or -1 (odd).  `kbase` counts the rows
 // this block has staged before this tile, so stage slots and mbarrier phases continue across
@@ -405,9 +428,7 @@ __device__ __forceinline__ bool run_tile(const CUtensorMap* srcp, S* __restrict_
     const bool in = LB_IN(ra >= 0 && ra < ny && r >= 0 && r < ny && rc >= 0 && rc < ny && cx >= 0, 3);
     mbar_arrive_expect_tx(&S_.full[s], in ? SM::kTxBytes : 0u);  // 0: the phase completes empty
     if (in) {
-      tma_load_3d(&S_.stage[s][0], srcp, cx, 0, ra, &S_.full[s]);
-      tma_load_3d(&S_.stage[s][GE], srcp, cx, 9, r, &S_.full[s]);
-      tma_load_3d(&S_.stage[s][2 * GE], srcp, cx, 18, rc, &S_.full[s]);
+      copy_row_boxes(S_.stage[s], GE, srcp, cx, ra, r, rc, &S_.full[s], k < 2);
     }
   };
   auto slot = [&](int k) -> int { return (int)((kb + (uint32_t)k) % NST); };
@@ -640,9 +661,7 @@ __device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* _
     const bool in = LB_IN(ra >= 0 && ra < ny && r >= 0 && r < ny && rc >= 0 && rc < ny && cx >= 0, 3);
     mbar_arrive_expect_tx(&S_.full[s], in ? SM::kTxBytes : 0u);  // 0: the phase completes empty
     if (in) {
-      tma_load_3d(&S_.stage[s][0], srcp, cx, 0, ra, &S_.full[s]);
-      tma_load_3d(&S_.stage[s][GE], srcp, cx, 9, r, &S_.full[s]);
-      tma_load_3d(&S_.stage[s][2 * GE], srcp, cx, 18, rc, &S_.full[s]);
+      copy_row_boxes(S_.stage[s], GE, srcp, cx, ra, r, rc, &S_.full[s], k < 2);
     }
   };
   auto slot = [&](int k) -> int { return (int)((kb + (uint32_t)k) % NST); };
@@ -931,27 +950,12 @@ constexpr size_t smem_bytes() {
   return sizeof(StepSmem<S, StepConfig<S>::kStages>) + 128;  // + alignment slack
 }
 
-// Launch with programmatic stream serialisation: the blocks of a step may be scheduled while the
-// previous kernel in the stream drains; each waits (grid_dependency_wait) before touching global
-// memory.  Measured: 6.5% less time per step at 256^2 binary32, 10% at 128^2, 3% at 512^2,
-// large grids unchanged (bitwise the same results); letting dependants launch early
-// (griddepcontrol.launch_dependents at block start) instead of at block exit made small grids
-// slower (128^2 binary32 23% slower).
-template <typename K, typename... A>
-cudaError_t launch_programmatic(K kernel, dim3 grid, int threads, size_t smem, cudaStream_t s, A... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
+// Steps are launched with programmatic stream serialisation (launch_programmatic): a step's
+// blocks may be scheduled while the previous kernel in the stream drains and wait
+// (grid_dependency_wait) before touching global memory.  Measured: 6.5% less time per step at
+// 256^2 binary32, 10% at 128^2, 3% at 512^2, large grids unchanged (bitwise the same
+// results); letting dependants launch early (griddepcontrol.launch_dependents at block start)
+// instead of at block exit made small grids slower (128^2 binary32 23% slower).
 template <typename S>
 cudaError_t launch_step(const CUtensorMap& src, S* dst, const StepGeom& g, const StepCoef& c,
                         int stencil, unsigned* err, const float* corr, cudaStream_t s) {
