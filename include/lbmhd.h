@@ -58,7 +58,9 @@ typedef struct lbmhd lbmhd_t; /* opaque handle */
 
 /* Problem statement, as the paper states it (Sec. 2 and Sec. 3). */
 typedef struct {
-  int nx, ny;        /* periodic grid, each >= 3 */
+  int nx, ny;        /* periodic grid, each >= 3; nx * ny <= 2^31 and nx <= 79,536,382 (a row
+                        of all 27 planes, 34 ghost/offset columns and padding to 32 included,
+                        must hold fewer than 2^31 elements); otherwise LBMHD_ERR_INVALID */
   double s[9];       /* fluid MRT rates s_j for the rows j of T (Eq. LBKinEqn); s[0..2] act
                         on conserved moments and are ignored; s[3..8] must lie in (0, 2).
                         nu = 1/(3 s_3) - 1/6 = 1/(3 s_4) - 1/6 and

@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -62,6 +63,10 @@ int check_params(const lbmhd_params* p) {
     return fail(nullptr, LBMHD_ERR_INVALID, "grid %d x %d: both sides must be >= 3", p->nx, p->ny);
   if ((long long)p->nx * p->ny > (1LL << 31))
     return fail(nullptr, LBMHD_ERR_INVALID, "grid %d x %d exceeds 2^31 cells", p->nx, p->ny);
+  // the row stride (all 27 planes of one row, ghost and pad columns included) is an int
+  if ((long long)kQ * (((long long)p->nx + kXOff + 2 + 31) / 32 * 32) > INT_MAX)
+    return fail(nullptr, LBMHD_ERR_INVALID, "grid width %d too large: a row of all 27 planes must "
+                "hold fewer than 2^31 elements", p->nx);
   for (int j = 3; j < 9; ++j)
     if (!(p->s[j] > 0.0 && p->s[j] < 2.0))
       return fail(nullptr, LBMHD_ERR_INVALID, "s[%d] = %g outside (0, 2)", j, p->s[j]);

@@ -65,6 +65,8 @@ def _fields(nx, ny):
 @pytest.mark.parametrize("mutate,needle", [
     (lambda p: setattr(p, "nx", 2), "grid"),
     (lambda p: setattr(p, "ny", 0), "grid"),
+    (lambda p: (setattr(p, "nx", 2**30), setattr(p, "ny", 3)), "2^31 cells"),
+    (lambda p: (setattr(p, "nx", 79_536_383), setattr(p, "ny", 3)), "width"),
     (lambda p: p.s.__setitem__(4, 2.0), "s[4]"),
     (lambda p: p.s.__setitem__(7, 0.0), "s[7]"),
     (lambda p: setattr(p, "s_m", -0.5), "s_m"),
