@@ -93,7 +93,11 @@ int lbmhd_init_device(lbmhd_t** out, const lbmhd_params* p, const double* rho,
 /* Advance nsteps >= 0 time steps (one step = collide, then stream; Sec. 3).  Each step is one
  * launch of the fused kernel: pull-stream the 27 populations, form rho, J, B and their
  * gradients, build the filtered equilibria, relax (Eq. LBKinEqn / LBMagEqn in moment space),
- * store.  Enqueued on the handle's stream; returns without synchronising. */
+ * store.  Enqueued on the handle's stream; returns without synchronising.  The step kernels
+ * are programmatic dependent launches: their blocks may be scheduled while the previous kernel
+ * on the stream finishes, but they touch no global memory before it has completed, so the
+ * stream's order holds for all work before and after them.  A wait that runs out in a step
+ * (2 s) is reported as LBMHD_ERR_TIMEOUT by the next synchronising call. */
 int lbmhd_step(lbmhd_t* h, int nsteps);
 
 /* Macroscopic fields of the current (post-stream, pre-collision) populations: rho,
