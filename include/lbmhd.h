@@ -36,7 +36,10 @@ extern "C" {
 #endif
 
 #define LBMHD_OK 0
-#define LBMHD_ERR_INVALID (-1)  /* bad argument (checked on the host before any GPU work) */
+#define LBMHD_ERR_INVALID (-1)  /* bad argument (checked on the host before any GPU work);
+                                   in the bounds-checking build (liblbmhd_check.so, compiled
+                                   with -DLBMHD_BOUNDS_CHECK) also a failed index check in a
+                                   step kernel, reported by the next synchronising call */
 #define LBMHD_ERR_CUDA (-2)     /* a CUDA runtime call failed (message has the CUDA error) */
 #define LBMHD_ERR_OOM (-3)      /* device memory allocation failed */
 #define LBMHD_ERR_UNSTABLE (-4) /* diagnostics found NaN/Inf, rho <= 0 or |u| > 0.4 */
