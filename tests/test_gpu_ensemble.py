@@ -99,3 +99,44 @@ def test_member_handles_are_read_only():
         ens.step(3)
         d = lbmhd.lbmhd_diagnostics(ens.member(1))
         assert np.isfinite(d).all()
+
+
+@pytest.mark.slow
+def test_full_size_48_run_ensemble_sampled():
+    """The 48-run ensemble of the benchmark (16 each of 128^2, 512^2, 1024^2, binary32,
+    Delta = 2) in its autotuned launch configuration, through the graph path: one more
+    ensemble step must equal the oracle's single-cell collision of each sampled member's own
+    state at sampled cells (f_i(x + c_i) after the step = f*_i(x) before it), to 1e-7 as for
+    the single 2048^2 grid."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+    mem = bench.ensemble_members()
+    picks = (0, 15, 16, 31, 32, 47)
+    rng = np.random.default_rng(11)
+    with lbmhd.Ensemble(mem) as ens:
+        ens.step(4)
+        ens.autotune(trial_steps=4)
+        ens.step(36)  # one captured 32-step graph and 4 single launches
+        before = {i: ens.populations(i) for i in picks}
+        ens.step(1)
+        after = {i: ens.populations(i) for i in picks}
+    worst = 0.0
+    for i in picks:
+        p, _ = mem[i]
+        n = p.nx
+        s = np.array(list(p.s))
+        f, g = before[i][:9], before[i][9:].reshape(2, 9, n, n)
+        pts = [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (127, 5), (min(128, n - 1), n // 2),
+               (n // 2, 0)]
+        pts += [tuple(int(v) for v in rng.integers(0, n, 2)) for _ in range(25)]
+        for (x, y) in pts:
+            fs, gs = oracle.collide_cell(f, g, s, p.s_m, p.delta, x, y)
+            for q in range(9):
+                xd, yd = (x + cx[q]) % n, (y + cy[q]) % n
+                worst = max(worst, abs(after[i][q, yd, xd] - fs[q]), abs(after[i][9 + q, yd, xd] - gs[0, q]),
+                            abs(after[i][18 + q, yd, xd] - gs[1, q]))
+    assert worst < 1e-7, worst
