@@ -166,15 +166,15 @@ def test_static_correction_matches_oracle(precision, tol):
     assert np.max(np.abs(np.concatenate([fp, gp.reshape(18, ny, nx)]) - ref)) > 1e-6
 
 
+@pytest.mark.parametrize("n", [64, 256])  # 256: the learned-closure LES grid (256 tiles)
 @pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32])
-def test_closure_in_the_loop_matches_its_static_correction(precision):
+def test_closure_in_the_loop_matches_its_static_correction(precision, n):
     """The attached closure forms u, B and the features from the populations in binary32 inside
     its one fused network launch; the same correction by hand goes through the binary64 moments,
     the features entry point and the forward pass.  They differ only by the rounding of the
     features (and so, rarely, of their bf16 copies), so the corrected steps agree to a small
     fraction of the correction's own effect on the populations."""
     import torch
-    n = 64
     f = kh_jet(n, seed=5)
     s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
     p = lbmhd.make_params(n, n, s, sm, 2.0, precision)
