@@ -63,3 +63,25 @@ def test_single_process_defaults():
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.workload_name(2048, "fp32", 0.0) == "kh_jet_2048x2048_dns_fp32"
     assert bench.workload_name(256, "fp32", 2.0) == "kh_jet_256x256_les_delta2_fp32"
+
+
+def test_reference_arm_line_on_rank0():
+    """Rank 0 of the reference arm times the oracle and prints one JSON line with the contract's
+    keys; its e2e and cpu_baseline are the line's own value."""
+    import json
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "2", "--warmup", "1", "--n", "64"], env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
