@@ -85,3 +85,16 @@ def test_reference_arm_line_on_rank0():
     assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_traffic_key_ignores_comments_and_whitespace():
+    """The measured DRAM traffic is keyed by a hash of the kernel source that comment and
+    whitespace edits do not change, while any code edit does."""
+    sys.path.insert(0, ROOT)
+    import bench
+    code = "int f(int a) {\n  return a + 1;  // one\n}\n/* block */\n"
+    same = "int f(int a){return a+1;}\n// another comment\n/* a\n longer block */"
+    other = "int f(int a) { return a + 2; }"
+    assert bench.source_hash(code) == bench.source_hash(same)
+    assert bench.source_hash(code) != bench.source_hash(other)
+    assert len(bench.kernel_hash()) == 16
