@@ -12,6 +12,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -581,10 +582,12 @@ cudaError_t set_net_attributes() {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  static bool attr_set[64] = {};
-  if (dev < 64 && attr_set[dev]) return cudaSuccess;
+  // per device, once; handles may be driven from several host threads (setting the attribute
+  // twice is harmless, a plain flag read while another thread writes it is not)
+  static std::atomic<bool> attr_set[64] = {};
+  if (dev < 64 && attr_set[dev].load(std::memory_order_acquire)) return cudaSuccess;
   e = cudaFuncSetAttribute(net_tc_kernel<SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNetSmemBytes);
-  if (e == cudaSuccess && dev < 64) attr_set[dev] = true;
+  if (e == cudaSuccess && dev < 64) attr_set[dev].store(true, std::memory_order_release);
   return e;
 }
 
