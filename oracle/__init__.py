@@ -2,8 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline / reference legs of ``bench.py`` may import this package.  The product path
-(the CUDA library and its binding) never imports or links it, and this package imports
-nothing from the product.
+(the CUDA library and its binding) never imports or links it.  Its one import from the
+product's package is the seeded input generator ``paper_1705_09807_gb300.inputs`` (used by
+``closure.init_params`` for its random weights), which holds none of the method's arithmetic.
 
 The arithmetic lives in ``lbmhd_oracle.c`` (plain C, binary64, ``-O2 -ffp-contract=off``);
 this module builds it with gcc on first use and marshals numpy arrays through ctypes.

@@ -85,3 +85,99 @@ def test_analytic_closure_on_sine_fields():
     np.testing.assert_allclose(a[1], kd * (d_jx ** 2 + d_by ** 2), atol=1e-17)
     np.testing.assert_allclose(a[2], kd * d_jx ** 2, atol=1e-17)
     np.testing.assert_allclose(a[3], kd * d_jx * d_by, atol=1e-17)
+
+
+# ------------------------------------------------------------------ the corrected step
+# The analytic closure a0..a3 is exactly the Delta^2/12 part of the filtered equilibria
+# (Eqs. FilterExampleSmall/Large, density gradients dropped as in Sec. 3), written per
+# subgrid term.  So one step with Delta = 0 plus the correction a (taken on the same state,
+# central differences) must equal one step with Delta = 2 (the oracle's filt_ratio/filt_prod
+# route), and each correction channel must land in the equilibrium moments where the k-terms
+# of its own products land: c0 in M_3, c1 in M_4, c2 in M_7 and M_8 (times -3), c3 in the
+# electric field of N^eq.  This pins oracle_step_corrected against the Delta^2 code path.
+
+import oracle as _or
+from paper_1705_09807_gb300.inputs import smooth_random_fields as _smooth
+
+_CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+_CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+
+
+def _generic_state(nx=13, ny=11, seed=21):
+    """A non-equilibrium state with O(1e-2) gradients: equilibria of smooth random fields
+    advanced by three plain steps."""
+    fields = _smooth(nx, ny, seed, amp_u=0.04, amp_b=0.04, amp_rho=0.02)
+    f, g = _or.init(*fields)
+    return _or.step(f, g, _or.srt_rates(0.01), _or.rate_from_diffusivity(0.01), 0.0, 3)
+
+
+def _post_collision(f, g):
+    """Undo the streaming of a one-step result: f*_i(x) = f_i(x + c_i)."""
+    fs = np.stack([np.roll(f[i], (-_CY[i], -_CX[i]), axis=(0, 1)) for i in range(9)])
+    gs = np.stack([np.stack([np.roll(g[a, i], (-_CY[i], -_CX[i]), axis=(0, 1)) for i in range(9)])
+                   for a in range(2)])
+    return fs, gs
+
+
+def _analytic_of(f, g, delta):
+    rho, ux, uy, bx, by = _or.moments(f, g)
+    return oc.analytic(rho, rho * ux, rho * uy, bx, by, delta)
+
+
+_RATES = {"srt": (_or.srt_rates(0.01), _or.rate_from_diffusivity(0.02)),
+          "mrt": (np.array([1.0, 1.0, 1.0, 1.6, 1.3, 1.1, 1.2, 1.45, 0.9]), 1.7)}
+
+
+@pytest.mark.parametrize("rates", ["srt", "mrt"])
+def test_corrected_step_with_analytic_terms_equals_filtered_step(rates):
+    s, sm = _RATES[rates]
+    f, g = _generic_state()
+    corr = _analytic_of(f, g, 2.0)
+    assert np.abs(corr).max() > 1e-5  # the terms are far above the tolerance below
+    f1, g1 = _or.step_corrected(f, g, s, sm, 0.0, 1, corr, stencil=0)
+    f2, g2 = _or.step(f, g, s, sm, 2.0, 1, stencil=0)
+    np.testing.assert_allclose(f1, f2, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(g1, g2, rtol=0, atol=1e-15)
+    # and the correction is not a no-op: the plain Delta = 0 step differs by far more
+    f0, _ = _or.step(f, g, s, sm, 0.0, 1, stencil=0)
+    assert np.abs(f0 - f2).max() > 1e-7
+
+
+@pytest.mark.parametrize("rates", ["srt", "mrt"])
+def test_each_correction_channel_lands_in_its_own_moments(rates):
+    """Channel q alone moves exactly the post-collision moments that the Delta^2 terms of its
+    products move (rows of Eq. FluidTMatrix / Eq. MagTMatrix), with the same sign, and no other."""
+    s, sm = _RATES[rates]
+    T = oc_tables()["T"]
+    Tm = oc_tables()["Tm"]
+    f, g = _generic_state(seed=22)
+    a = _analytic_of(f, g, 2.0)
+
+    def moments_after(fn):
+        fs, gs = _post_collision(*fn())
+        M = np.einsum("ji,ixy->jxy", T, fs)
+        N = np.einsum("ji,aixy->ajxy", Tm, gs)
+        return M, N
+
+    M0, N0 = moments_after(lambda: _or.step(f, g, s, sm, 0.0, 1))
+    M2, N2 = moments_after(lambda: _or.step(f, g, s, sm, 2.0, 1))
+    dM, dN = M2 - M0, N2 - N0  # what the Delta^2 terms do, row by row
+    rows = {0: [3], 1: [4], 2: [7, 8], 3: []}
+    for q in range(4):
+        corr = np.zeros_like(a)
+        corr[q] = a[q]
+        Mq, Nq = moments_after(lambda: _or.step_corrected(f, g, s, sm, 0.0, 1, corr))
+        want_M = np.zeros_like(dM)
+        want_M[rows[q]] = dM[rows[q]]
+        want_N = dN if q == 3 else np.zeros_like(dN)
+        np.testing.assert_allclose(Mq - M0, want_M, rtol=0, atol=1e-15, err_msg=f"channel {q}")
+        np.testing.assert_allclose(Nq - N0, want_N, rtol=0, atol=1e-15, err_msg=f"channel {q}")
+        moved = [j for j in range(9) if np.abs(Mq[j] - M0[j]).max() > 1e-12]
+        assert moved == rows[q], (q, moved)
+    # every fluid row the Delta^2 terms move belongs to exactly one channel
+    assert [j for j in range(9) if np.abs(dM[j]).max() > 1e-12] == [3, 4, 7, 8]
+    assert np.abs(dN).max() > 1e-9
+
+
+def oc_tables():
+    return _or.tables()
