@@ -289,13 +289,25 @@ int64_t lbmhd_step_count(const lbmhd_t* h);
  * per 4096 cells) is a fixed 352 KiB device array of the library, resident on every GPU that
  * loads the library until the process exits.  Hence at most 4096 x 4096 = 16,777,216 cells;
  * larger grids, sides < 3 and NULL pointers return LBMHD_ERR_INVALID (see lbmhd_last_error(NULL)).
- * The first call on a device looks up that array's device address (once per device, with the
- * device current); make that first call before any stream capture.  All calls share the one
+ * The first call in a device's context looks up that array's device address (with the device
+ * current) and keeps it for that context; make that first call before any stream capture.  A
+ * call in a new context of the same device (after cudaDeviceReset, say) looks it up again,
+ * so the first call after such a reset must also come before any capture.  All calls share the one
  * array, so calls that overlap on the GPU (different streams, no ordering) race and may return
  * wrong values; each call overwrites every record it reads, so nothing needs clearing. */
 int lbmhd_diagnostics_fields_noalloc(const double* rho, const double* ux, const double* uy,
                                      const double* bx, const double* by, int nx, int ny,
                                      double* out, void* stream);
+
+/* Measured binary64 FMA rate of the current device, the arithmetic ceiling of the LBMHD_FP64
+ * step (about 216 binary64 instructions per cell update; the paper states no precision or
+ * hardware, so this is a property of the GPU that runs it, not of the method).  One warm-up
+ * launch, then `repeats` timed launches of (SMs x 8) blocks x 256 threads, each thread running
+ * 8 independent chains x <- x a + b for `iters` iterations; *dfma_per_second = DFMAs per launch
+ * / median CUDA-event time (one DFMA = 2 flops).  Allocates a small device buffer and a stream
+ * for the call and frees them; synchronises.  iters in [1, 2^20], repeats in [1, 100], else
+ * LBMHD_ERR_INVALID; CUDA failures return LBMHD_ERR_CUDA (message: lbmhd_last_error(NULL)). */
+int lbmhd_probe_fp64_fma_rate(int iters, int repeats, double* dfma_per_second);
 
 /* Message for the last error on h, or for the calling thread's last handle-less call when
  * h is NULL.  Never NULL; valid until the next call on the same handle / thread. */

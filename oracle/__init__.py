@@ -146,6 +146,18 @@ def step(f, g, s, s_m, delta, nsteps, stencil=0, nthreads=1):
     return f, g
 
 
+def step_inplace(f, g, s, s_m, delta, nsteps, stencil=0, nthreads=1) -> None:
+    """``step`` advancing ``f`` and ``g`` in place (C-contiguous float64 arrays, no copy): for
+    timing the oracle on large grids, where a copy of the state would cost as much as a step."""
+    if not (f.dtype == np.float64 and g.dtype == np.float64 and f.flags["C_CONTIGUOUS"]
+            and g.flags["C_CONTIGUOUS"] and f.flags["WRITEABLE"] and g.flags["WRITEABLE"]):
+        raise ValueError("step_inplace needs writeable C-contiguous float64 arrays")
+    ny, nx = f.shape[1:]
+    s = _arr(s, 9)
+    _check(_load().oracle_step(nx, ny, _p(s), s_m, delta, stencil, _p(f), _p(g), nsteps,
+                               nthreads), "step")
+
+
 def step_corrected(f, g, s, s_m, delta, nsteps, corr, stencil=0, nthreads=1):
     """``step`` with a fixed additive correction corr[4, ny, nx] of the four subgrid terms
     (xy stress, normal-stress difference, trace, electric field) at every cell and step."""

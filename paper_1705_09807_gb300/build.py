@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbmhd.so")
 SOURCES = ["lbmhd_step.cu", "lbmhd_aux.cu", "lbmhd_api.cu", "lbmhd_noalloc.cu", "lbmhd_analysis.cu",
-           "lbmhd_ensemble.cu", "lbmhd_closure.cu"]
+           "lbmhd_ensemble.cu", "lbmhd_closure.cu", "lbmhd_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

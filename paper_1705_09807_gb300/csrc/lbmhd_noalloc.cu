@@ -10,6 +10,7 @@
 // The reduction is the same as lbmhd_diagnostics' (sums, maxima and the instability flag),
 // split over blocks of kCellsPerBlock consecutive cells, then combined by one block in block
 // order, so the result is bitwise reproducible for a given grid.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -33,7 +34,6 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_partials[kMaxBlocks * kSlots];
 
 std::mutex g_setup_mutex;
-double* g_partials_addr[kMaxDevices] = {};
 
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
@@ -119,14 +119,57 @@ int set_error(int code, const char* msg) {
   return code;
 }
 
-// Device address of g_partials on the current device, looked up once per device.
+// Driver calls that identify the current context, reached through the runtime's driver entry
+// point (the library does not link libcuda).  cuCtxGetId gives a context an identifier that is
+// unique for the life of the process, so a context that was destroyed and re-created (for
+// example after cudaDeviceReset) is told apart from its predecessor even if its handle value is
+// reused.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+template <typename F>
+F driver_fn(const char* name, int version) {
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &f, version, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return reinterpret_cast<F>(f);
+}
+
+// Identifier of the calling thread's current context; false if it cannot be had (no current
+// context yet, or a driver without cuCtxGetId), in which case the caller looks the address up
+// afresh.
+bool current_context_id(unsigned long long* id) {
+  static const CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent", 4000);
+  static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId", 12000);
+  if (!get_current || !get_id) return false;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+struct PartialsAddr {
+  double* ptr = nullptr;
+  unsigned long long ctx_id = 0;
+};
+PartialsAddr g_partials_addr[kMaxDevices];
+
+// Device address of g_partials in the current device's current context.  It is looked up with
+// cudaGetSymbolAddress on the first call in a context (which also loads the library's module
+// into that context if it is not loaded yet) and cached with the context's identifier; a call
+// in another context -- a different device, or the same device after its primary context was
+// reset -- looks it up again instead of using a stale address.
 int partials_address(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_error(LBMHD_ERR_CUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return set_error(LBMHD_ERR_INVALID, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_partials_addr[dev]) {
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id);
+  PartialsAddr& a = g_partials_addr[dev];
+  if (!(have_id && a.ptr && a.ctx_id == id)) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_partials);
     if (e != cudaSuccess || !p) {
@@ -135,9 +178,11 @@ int partials_address(double** out) {
                cudaGetErrorString(e));
       return set_error(LBMHD_ERR_CUDA, buf);
     }
-    g_partials_addr[dev] = static_cast<double*>(p);
+    a.ptr = static_cast<double*>(p);
+    // the lookup above makes the primary context current if it was not yet
+    a.ctx_id = current_context_id(&id) ? id : 0;
   }
-  *out = g_partials_addr[dev];
+  *out = a.ptr;
   return LBMHD_OK;
 }
 

@@ -98,6 +98,7 @@ def load_library(path: str | None = None):
                 ctypes.c_size_t, ctypes.c_void_p]),
             "lbmhd_energy_spectrum": (ctypes.c_int, [_H, ctypes.c_int, _D, _D]),
             "lbmhd_launch_count": (ctypes.c_uint64, [_H]),
+            "lbmhd_probe_fp64_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _D]),
             "lbmhd_ensemble_create": (ctypes.c_int, [ctypes.POINTER(_H), ctypes.c_int, P,
                                                      ctypes.POINTER(_D), ctypes.c_void_p]),
             "lbmhd_ensemble_step": (ctypes.c_int, [_H, ctypes.c_int]),
@@ -318,6 +319,13 @@ def lbmhd_launch_count(h) -> int:
 
 def lbmhd_step_count(h) -> int:
     return int(load_library().lbmhd_step_count(h))
+
+
+def lbmhd_probe_fp64_fma_rate(iters: int = 4096, repeats: int = 5) -> float:
+    """Measured binary64 FMA instructions per second of the current GPU."""
+    v = ctypes.c_double(0.0)
+    _check(load_library().lbmhd_probe_fp64_fma_rate(iters, repeats, ctypes.byref(v)))
+    return v.value
 
 
 def lbmhd_last_error(h=None) -> str:

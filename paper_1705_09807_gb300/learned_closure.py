@@ -97,8 +97,9 @@ def a_priori(closure, X, T):
 
 def a_posteriori(closure, n, r, seed, nu_dns, delta, checkpoints, precision=lbmhd.LBMHD_FP32):
     """LES on the coarse grid from the box-filtered DNS initial fields, with the analytic closure
-    alone and with the network attached, against the filtered DNS: relative L2 of total-energy
-    spectra (shells 1 .. m/2 - 1) at the DNS checkpoints (coarse step = DNS step / r)."""
+    alone, with the network attached and with no closure at all (Delta = 0, the unfiltered
+    coarse run), against the filtered DNS: relative L2 of total-energy spectra (shells
+    1 .. m/2 - 1) at the DNS checkpoints (coarse step = DNS step / r)."""
     import torch
     m = n // r
     u0, b0 = run_params(seed)
@@ -113,6 +114,7 @@ def a_posteriori(closure, n, r, seed, nu_dns, delta, checkpoints, precision=lbmh
     dns = lbmhd.Lbmhd(lbmhd.lbmhd_params_srt(n, n, nu_dns, nu_dns, 0.0, precision), *fields)
     les = lbmhd.Lbmhd(lbmhd.lbmhd_params_srt(m, m, nu_c, nu_c, delta, precision), *coarse, device=True)
     net = lbmhd.Lbmhd(lbmhd.lbmhd_params_srt(m, m, nu_c, nu_c, delta, precision), *coarse, device=True)
+    bare = lbmhd.Lbmhd(lbmhd.lbmhd_params_srt(m, m, nu_c, nu_c, 0.0, precision), *coarse, device=True)
     closure.attach(net.h)
     nb = m // 2 + 1
     work = torch.empty(lbmhd.lbmhd_energy_spectrum_work_bytes(m), dtype=torch.uint8, device="cuda")
@@ -126,6 +128,7 @@ def a_posteriori(closure, n, r, seed, nu_dns, delta, checkpoints, precision=lbmh
         dns.step(steps)
         les.step(steps // r)
         net.step(steps // r)
+        bare.step(steps // r)
         done += steps
         dns.moments_device(fm)
         torch.cuda.synchronize()
@@ -135,14 +138,14 @@ def a_posteriori(closure, n, r, seed, nu_dns, delta, checkpoints, precision=lbmh
         torch.cuda.synchronize()
         ref = (ek + em).cpu().numpy()
         rec = {"dns_step": done}
-        for name, sim in (("analytic", les), ("analytic_plus_network", net)):
+        for name, sim in (("analytic", les), ("analytic_plus_network", net), ("no_closure", bare)):
             k_, m_ = sim.spectrum(nb)
             tot = k_ + m_
             sl = slice(1, m // 2)
             rec[name] = float(np.linalg.norm(tot[sl] - ref[sl]) / np.linalg.norm(ref[sl]))
         out.append(rec)
     lbmhd.lbmhd_detach_closure(net.h)
-    for sim in (dns, les, net):
+    for sim in (dns, les, net, bare):
         sim.free()
     return out
 

@@ -6,6 +6,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
@@ -98,3 +99,14 @@ def test_traffic_key_ignores_comments_and_whitespace():
     assert bench.source_hash(code) == bench.source_hash(same)
     assert bench.source_hash(code) != bench.source_hash(other)
     assert len(bench.kernel_hash()) == 16
+
+
+def test_timed_windows_cover_five_repeats_and_one_second():
+    """The K-step interval is timed at least 5 times and for at least one second in all,
+    whatever K is (a 20-step run of a 0.14 ms step needs hundreds of windows)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.windows_needed(0.14, 20) == int(np.ceil(1.0 / (0.14e-3 * 20)))
+    assert bench.windows_needed(0.14, 20) * 20 * 0.14e-3 >= 1.0
+    assert bench.windows_needed(1.8, 20000) == 5       # long windows: the five repeats decide
+    assert bench.windows_needed(0.0, 20) >= 5           # a zero estimate does not divide by zero
