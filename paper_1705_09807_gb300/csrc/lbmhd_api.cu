@@ -235,18 +235,22 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
 }
 
 // One fused step from copy `from` into copy `to` (with the subgrid correction planes `corr`,
-// or none).
+// or none).  The bands' marching direction alternates with `from` (binary64 / binary32), so each
+// band starts a step on the rows it wrote last, still in L2: at 2048^2 binary32 that cut the DRAM
+// reads of a step from 471 MB to 427 MB (ncu without its L2 flush) and the time by 0.5%; the
+// binary16 form, bound by latency rather than memory, ran 0.7% slower with it and keeps a fixed
+// direction.
 cudaError_t launch_one(lbmhd_t* h, int from, int to, const float* corr = nullptr) {
   switch (h->precision) {
     case LBMHD_FP64:
       return launch_step_f64(h->tmap[from], (double*)h->pops[to], h->geom, h->coef,
-                             h->p.grad_stencil, h->err_flag, corr, h->stream);
+                             h->p.grad_stencil, h->err_flag, corr, from, h->stream);
     case LBMHD_FP32:
       return launch_step_f32(h->tmap[from], (float*)h->pops[to], h->geom, h->coef,
-                             h->p.grad_stencil, h->err_flag, corr, h->stream);
+                             h->p.grad_stencil, h->err_flag, corr, from, h->stream);
     default:
       return launch_step_f16(h->tmap[from], (__half*)h->pops[to], h->geom, h->coef,
-                             h->p.grad_stencil, h->err_flag, corr, h->stream);
+                             h->p.grad_stencil, h->err_flag, corr, 0, h->stream);
   }
 }
 

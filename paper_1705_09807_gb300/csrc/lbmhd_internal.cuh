@@ -101,16 +101,18 @@ struct StepGeom {
 // source copy (box {box_width(elem), 1, 9}); dst is the other copy.  *err receives 1 if a pipeline wait
 // timed out (the kernel then stops early; the state is not valid).  corr (may be NULL): four
 // binary32 planes [4][ny][nx] added to the subgrid terms of the collision (xy stress, normal
-// stress difference, trace, electric field); not offered for binary16 storage.
+// stress difference, trace, electric field); not offered for binary16 storage.  flip (0 / 1)
+// reverses the bands' marching directions; callers pass the source copy's index so that the
+// direction alternates from step to step (results do not depend on it).
 cudaError_t launch_step_f64(const CUtensorMap& src, double* dst, const StepGeom& g,
                             const StepCoef& c, int stencil, unsigned* err, const float* corr,
-                            cudaStream_t s);
+                            int flip, cudaStream_t s);
 cudaError_t launch_step_f32(const CUtensorMap& src, float* dst, const StepGeom& g,
                             const StepCoef& c, int stencil, unsigned* err, const float* corr,
-                            cudaStream_t s);
+                            int flip, cudaStream_t s);
 cudaError_t launch_step_f16(const CUtensorMap& src, __half* dst, const StepGeom& g,
                             const StepCoef& c, int stencil, unsigned* err, const float* corr,
-                            cudaStream_t s);
+                            int flip, cudaStream_t s);
 // Rows per block for the grid and precision (one wave of resident blocks when possible).
 int step_band_rows(int nx, int ny, int precision, int num_sms);
 // Opt the step kernels in to their dynamic shared memory (once per process and device).

@@ -823,17 +823,21 @@ __device__ __forceinline__ bool run_any_tile(const CUtensorMap* srcp, S* __restr
 }
 
 // One grid: block (strip, band) = one tile.  CORR: add the correction planes corr[4][ny][nx].
+// flip (0 / 1, the source copy's index, so it alternates from step to step) reverses every
+// band's marching direction: a band then starts each step at the rows it (and its neighbour)
+// wrote last in the previous step, which are still in L2 (about the last 5 rows per band at
+// 2048^2 binary32), instead of at the far end, long evicted.
 template <typename S, int ISO, int NST, int MINB, bool CORR = false>
 __global__ void __launch_bounds__(step_threads<S>(), MINB)
     fused_step_kernel(const __grid_constant__ CUtensorMap src, S* __restrict__ dst, StepGeom g,
                       KCoef<typename ArithOf<S>::type> c, unsigned* __restrict__ err,
-                      const float* __restrict__ corr) {
+                      const float* __restrict__ corr, int flip) {
   if ((int)blockIdx.y * g.band >= g.ny) return;  // uniform per block
   init_stage_barriers(step_smem<S, NST>(), &src);
   grid_dependency_wait();  // the previous step has written src (and read dst)
   uint32_t kbase = 0;
-  run_any_tile<S, ISO, NST, CORR>(&src, dst, g, c, blockIdx.x * kStepThreads, blockIdx.y * g.band, blockIdx.y,
-                                  kbase, err, corr);
+  run_any_tile<S, ISO, NST, CORR>(&src, dst, g, c, blockIdx.x * kStepThreads, blockIdx.y * g.band,
+                                  (int)blockIdx.y + flip, kbase, err, corr);
 }
 
 // Ensemble: every member grid advances one step in this launch.  work[i] = {member, x0, y0,
@@ -864,7 +868,10 @@ __global__ void __launch_bounds__(step_threads<S>(), MINB)
   while (w < nwork) {
     const int4 it = work[w];
     const EnsembleMember<S>& mb = members[it.x];
-    if (!run_any_tile<S, ISO, NST>(&mb.map[parity], mb.pops[parity ^ 1], mb.g, mb.c, it.y, it.z, it.w,
+    // the march direction alternates with the step (parity) as for single grids: not for
+    // binary16 storage
+    const int flip = sizeof(S) == 2 ? 0 : parity;
+    if (!run_any_tile<S, ISO, NST>(&mb.map[parity], mb.pops[parity ^ 1], mb.g, mb.c, it.y, it.z, it.w + flip,
                                    kbase, err))
       return;
     if (queue) {
@@ -958,7 +965,7 @@ constexpr size_t smem_bytes() {
 // instead of at block exit made small grids slower (128^2 binary32 23% slower).
 template <typename S>
 cudaError_t launch_step(const CUtensorMap& src, S* dst, const StepGeom& g, const StepCoef& c,
-                        int stencil, unsigned* err, const float* corr, cudaStream_t s) {
+                        int stencil, unsigned* err, const float* corr, int flip, cudaStream_t s) {
   dim3 grid((g.nx + kStepThreads - 1) / kStepThreads, (g.ny + g.band - 1) / g.band);
   auto k = cast_coef<typename ArithOf<S>::type>(c);
   const int nt = step_threads<S>();
@@ -967,12 +974,12 @@ cudaError_t launch_step(const CUtensorMap& src, S* dst, const StepGeom& g, const
     if constexpr (sizeof(S) == 2)
       return cudaErrorNotSupported;  // the correction is offered for binary64 / binary32 storage
     else
-      return stencil == 1 ? launch_programmatic(kernel_ptr<S, 1, true>(), grid, nt, sm, s, src, dst, g, k, err, corr)
-                          : launch_programmatic(kernel_ptr<S, 0, true>(), grid, nt, sm, s, src, dst, g, k, err, corr);
+      return stencil == 1 ? launch_programmatic(kernel_ptr<S, 1, true>(), grid, nt, sm, s, src, dst, g, k, err, corr, flip)
+                          : launch_programmatic(kernel_ptr<S, 0, true>(), grid, nt, sm, s, src, dst, g, k, err, corr, flip);
   }
   const float* none = nullptr;
-  return stencil == 1 ? launch_programmatic(kernel_ptr<S, 1>(), grid, nt, sm, s, src, dst, g, k, err, none)
-                      : launch_programmatic(kernel_ptr<S, 0>(), grid, nt, sm, s, src, dst, g, k, err, none);
+  return stencil == 1 ? launch_programmatic(kernel_ptr<S, 1>(), grid, nt, sm, s, src, dst, g, k, err, none, flip)
+                      : launch_programmatic(kernel_ptr<S, 0>(), grid, nt, sm, s, src, dst, g, k, err, none, flip);
 }
 
 template <typename S, int ISO>
@@ -1056,20 +1063,20 @@ cudaError_t prepare_step_kernels() {
 
 cudaError_t launch_step_f64(const CUtensorMap& src, double* dst, const StepGeom& g,
                             const StepCoef& c, int stencil, unsigned* err, const float* corr,
-                            cudaStream_t s) {
-  return launch_step<double>(src, dst, g, c, stencil, err, corr, s);
+                            int flip, cudaStream_t s) {
+  return launch_step<double>(src, dst, g, c, stencil, err, corr, flip, s);
 }
 
 cudaError_t launch_step_f32(const CUtensorMap& src, float* dst, const StepGeom& g,
                             const StepCoef& c, int stencil, unsigned* err, const float* corr,
-                            cudaStream_t s) {
-  return launch_step<float>(src, dst, g, c, stencil, err, corr, s);
+                            int flip, cudaStream_t s) {
+  return launch_step<float>(src, dst, g, c, stencil, err, corr, flip, s);
 }
 
 cudaError_t launch_step_f16(const CUtensorMap& src, __half* dst, const StepGeom& g,
                             const StepCoef& c, int stencil, unsigned* err, const float* corr,
-                            cudaStream_t s) {
-  return launch_step<__half>(src, dst, g, c, stencil, err, corr, s);
+                            int flip, cudaStream_t s) {
+  return launch_step<__half>(src, dst, g, c, stencil, err, corr, flip, s);
 }
 
 size_t ensemble_member_bytes(int precision) {

@@ -219,14 +219,27 @@ def test_training_lowers_the_loss():
 
 
 def test_trained_network_beats_the_analytic_closure_a_priori():
-    """What the network gains: trained on box-filtered fine runs (256^2 -> 64^2, three seeded
-    jets), it must reduce the held-out error of the subgrid terms below the analytic closure's
-    (the a-priori ratio |T - net(X)| / |T| < 0.8 on every channel of an unseen run)."""
+    """What the network gains, a priori and a posteriori.  Trained on box-filtered fine runs
+    (256^2 -> 64^2, three seeded jets), it must reduce the held-out error of the subgrid terms
+    far below the analytic closure's (measured ratio |T - net(X)| / |T| of 0.15 / 0.19 / 0.19 /
+    0.19 on the four channels of an unseen run; asserted < 0.4).
+
+    A posteriori (the 64^2 LES run from the filtered initial fields against the filtered DNS,
+    relative L2 of the total-energy spectra at DNS step 400) the gain is almost nothing: measured
+    2.0544e-3 with the network against 2.0597e-3 with the analytic closure alone (0.26% lower)
+    and 2.0597e-3 with no closure at all (the analytic terms change it by 1e-8 relative: in this
+    resolved, low-Re run the subgrid terms barely move the flow).  The assertions record that
+    result: the network lowers the error by between 0.05% and 1%, and the analytic closure and
+    no closure agree to 1e-5."""
     from paper_1705_09807_gb300 import learned_closure as lc
     res = lc.run(n=256, r=4, nu_dns=8e-3, delta=2.0, train_seeds=range(3), test_seed=100,
                  snapshots=(200, 400, 600, 800), iters=400, batch=4, lr=2e-3)
     assert res["loss_last"] < 0.5 * res["loss_first"]
     ratio = res["a_priori_test"]["ratio"]
-    assert max(ratio) < 0.8, ratio
+    assert max(ratio) < 0.4, ratio
+    assert len(res["a_posteriori_test"]) >= 1
     for rec in res["a_posteriori_test"]:
-        assert np.isfinite(rec["analytic"]) and np.isfinite(rec["analytic_plus_network"])
+        a, net, none = rec["analytic"], rec["analytic_plus_network"], rec["no_closure"]
+        assert 1e-3 < a < 5e-3, rec  # the coarse run tracks the filtered DNS to ~0.2%
+        assert 0.99 < net / a < 0.9995, rec
+        assert abs(a / none - 1.0) < 1e-5, rec
