@@ -41,7 +41,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS and % HBM roofline per LES-LB-MHD step vs plain FP64 step, at stated L2 err"
-BYTES_PER_CELL = {"fp16": 108, "fp32": 216, "fp64": 432}   # 27 populations read + 27 written
+# 27 populations read + 27 written (binary16 relative to the local velocity: + 2 velocity planes)
+BYTES_PER_CELL = {"fp16": 108, "fp16rel": 116, "fp32": 216, "fp64": 432}
 FP64_INSTR_PER_CELL = 216  # binary64 instructions per cell-update of the FP64 step (ncu)
 MIN_WINDOWS = 5          # timed K-step windows, at least
 MIN_TIMED_S = 1.0        # and at least this much timed time in all
@@ -64,7 +65,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=2048, help="grid side (default: the 2048^2 workload)")
-    ap.add_argument("--precision", choices=["fp16", "fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp16", "fp16rel", "fp32", "fp64"], default="fp32")
     ap.add_argument("--delta", type=float, default=0.0)
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--only", choices=["closure", "ensemble"],
@@ -211,7 +212,8 @@ def peaks():
 def make_sim(n, precision, delta, stream=None, nu=NU, delta_frac=1 / 32, stencil=0):
     from paper_1705_09807_gb300 import lbmhd
     from paper_1705_09807_gb300.inputs import kh_jet
-    prec = {"fp16": lbmhd.LBMHD_FP16, "fp32": lbmhd.LBMHD_FP32, "fp64": lbmhd.LBMHD_FP64}[precision]
+    prec = {"fp16": lbmhd.LBMHD_FP16, "fp16rel": lbmhd.LBMHD_FP16_REL, "fp32": lbmhd.LBMHD_FP32,
+            "fp64": lbmhd.LBMHD_FP64}[precision]
     p = lbmhd.lbmhd_params_srt(n, n, nu, nu, delta, prec)
     p.cuda_stream = stream
     p.grad_stencil = stencil
@@ -410,8 +412,10 @@ def run_ours(a, rank, ws, local):
 
 def side_measurements(n, a):
     """Beside the timed workload: the plain FP64 step on the same grid (binary64-ALU bound),
-    the FP16-storage form, the LES form (Delta = 2), the precision forms' relative L2 against an
-    FP64 GPU run of the 4096^2 precision configuration, and the 256^2 LES grid."""
+    the binary16 storage forms (plain and relative to the local velocity), the LES form
+    (Delta = 2), every form on the 4096^2 grid of the precision configuration, the precision
+    forms' relative L2 against an FP64 GPU run of that configuration, the 256^2 LES grid with
+    and without the learned closure, and the 48-run ensemble."""
     import torch
     res = {}
 
@@ -422,14 +426,15 @@ def side_measurements(n, a):
         sim.free()
         return ms
 
-    # binary64 ALU ceiling, measured now on this GPU (lbmhd_probe_fp64_fma_rate: SMs x 8 blocks
-    # x 256 threads, 8 independent DFMA chains each, median of 5 launches)
+    # binary64 ALU ceiling, measured now on this GPU (lbmhd_probe_fp64_fma_rate: the fastest of
+    # three shapes of independent DFMA chains, median of 5 launches each)
     from paper_1705_09807_gb300 import lbmhd
     dfma_rate = lbmhd.lbmhd_probe_fp64_fma_rate(4096, 5)
     res["fp64_fma_probe"] = {"dfma_per_s": round(dfma_rate, -6), "tflops": round(2 * dfma_rate / 1e12, 4),
-                             "how": "lbmhd_probe_fp64_fma_rate(iters=4096, repeats=5): SMs x 8 blocks "
-                                    "x 256 threads, 8 independent DFMA chains per thread, median "
-                                    "CUDA-event time of 5 launches after one warm-up launch"}
+                             "how": "lbmhd_probe_fp64_fma_rate(iters=4096, repeats=5): 4 / 8 / 16 "
+                                    "independent DFMA chains per thread in SMs x 16 / 8 / 4 blocks of "
+                                    "256 threads, median CUDA-event time of 5 launches after one "
+                                    "warm-up launch, fastest shape"}
 
     def fp64_line(nn, ms64):
         # 216 binary64 instructions per cell-update (ncu: 121 DADD + 64 DFMA + 31 DMUL); the ALU
@@ -449,11 +454,15 @@ def side_measurements(n, a):
 
     res["fp64_step"] = fp64_line(n, rate(make_sim(n, "fp64", a.delta)[0], 100))
     res["fp16_step"] = hbm_line(n, rate(make_sim(n, "fp16", a.delta)[0], 1000), "fp16")
+    # binary16 relative to the local velocity: 29 planes (116 B per cell update)
+    res["fp16rel_step"] = hbm_line(n, rate(make_sim(n, "fp16rel", a.delta)[0], 1000), "fp16rel")
     # the precision configuration's grid: 4096^2 KH jet, d = N/64, Delta = 2, in every form
     n3, nu3 = 4096, 4e-3
     res["grid_4096_les_delta2"] = {
         "fp32": hbm_line(n3, rate(make_sim(n3, "fp32", 2.0, nu=nu3, delta_frac=1 / 64)[0], 400), "fp32"),
         "fp16": hbm_line(n3, rate(make_sim(n3, "fp16", 2.0, nu=nu3, delta_frac=1 / 64)[0], 600), "fp16"),
+        "fp16rel": hbm_line(n3, rate(make_sim(n3, "fp16rel", 2.0, nu=nu3, delta_frac=1 / 64)[0], 500),
+                            "fp16rel"),
         "fp64": fp64_line(n3, rate(make_sim(n3, "fp64", 2.0, nu=nu3, delta_frac=1 / 64)[0], 30))}
     msl = rate(make_sim(n, "fp32", 2.0)[0], 1000)
     res["fp32_les_delta2"] = {"mlups": round(n * n / msl / 1e3, 2)}
@@ -463,14 +472,14 @@ def side_measurements(n, a):
     # paper's constant-Re viscosity at 4096^2 (4e-3; the configuration's 2e-4 diverges before
     # step 1000 in this SRT model)
     acc = {"workload": "kh_jet_4096x4096_les_delta2", "nu": nu3}
-    sims = {p: make_sim(n3, p, 2.0, nu=nu3, delta_frac=1 / 64)[0] for p in ("fp64", "fp32", "fp16")}
+    sims = {p: make_sim(n3, p, 2.0, nu=nu3, delta_frac=1 / 64)[0] for p in ("fp64", "fp32", "fp16", "fp16rel")}
     done = 0
     for t in (1000, 5000):
         for sim in sims.values():
             sim.step(t - done)
         done = t
         m64 = sims["fp64"].moments()
-        for p in ("fp32", "fp16"):
+        for p in ("fp32", "fp16", "fp16rel"):
             acc.setdefault(p, {})[str(t)] = field_errors(sims[p].moments(), m64)
     for sim in sims.values():
         sim.free()

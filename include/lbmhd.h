@@ -50,6 +50,13 @@ extern "C" {
 #define LBMHD_FP64 0 /* populations stored in binary64, collision in binary64 */
 #define LBMHD_FP32 1 /* f_i - w_i and g_i stored in binary32, collision in binary32 */
 #define LBMHD_FP16 2 /* f_i - w_i and g_i stored in binary16, collision in binary32 */
+#define LBMHD_FP16_REL 3 /* binary16 storage relative to the local velocity: f_i - w_i (1 + 3 c_i . U)
+                            and g_i, where U is the velocity of the cell that stored the value,
+                            itself stored in binary16 in two more planes (116 instead of 108 bytes
+                            per cell update); collision in binary32.  Removing the O(u) part of
+                            f_i before rounding resolves the density fluctuation that LBMHD_FP16
+                            rounds away.  Single grids only: ensembles, static corrections and
+                            the learned closure take the other forms. */
 
 /* Finite-difference stencils for d_beta (the paper leaves the discretisation open). */
 #define LBMHD_GRAD_CENTRAL 0   /* (a(x+e_beta) - a(x-e_beta)) / 2 */
@@ -63,7 +70,8 @@ typedef struct lbmhd lbmhd_t; /* opaque handle */
 typedef struct {
   int nx, ny;        /* periodic grid, each >= 3; nx * ny <= 2^31 and nx <= 79,536,382 (a row
                         of all 27 planes, 34 ghost/offset columns and padding to 32 included,
-                        must hold fewer than 2^31 elements); otherwise LBMHD_ERR_INVALID */
+                        must hold fewer than 2^31 elements; 74,051,102 for the 29 planes of
+                        LBMHD_FP16_REL); otherwise LBMHD_ERR_INVALID */
   double s[9];       /* fluid MRT rates s_j for the rows j of T (Eq. LBKinEqn); s[0..2] act
                         on conserved moments and are ignored; s[3..8] must lie in (0, 2).
                         nu = 1/(3 s_3) - 1/6 = 1/(3 s_4) - 1/6 and
@@ -72,7 +80,7 @@ typedef struct {
   double s_m;        /* magnetic SRT rate (Eq. LBMagEqn), in (0, 2); eta = 1/(3 s_m) - 1/6 */
   double delta;      /* filter width Delta in lattice units, >= 0; the Delta^2/12 terms of
                         Sec. 2.1; 0 gives plain (DNS) LB-MHD */
-  int precision;     /* LBMHD_FP64, LBMHD_FP32 or LBMHD_FP16 */
+  int precision;     /* LBMHD_FP64, LBMHD_FP32, LBMHD_FP16 or LBMHD_FP16_REL */
   int grad_stencil;  /* LBMHD_GRAD_CENTRAL or LBMHD_GRAD_ISOTROPIC */
   void* cuda_stream; /* cudaStream_t to run on; NULL: the handle creates its own stream */
 } lbmhd_params;
@@ -301,10 +309,11 @@ int lbmhd_diagnostics_fields_noalloc(const double* rho, const double* ux, const 
 
 /* Measured binary64 FMA rate of the current device, the arithmetic ceiling of the LBMHD_FP64
  * step (about 216 binary64 instructions per cell update; the paper states no precision or
- * hardware, so this is a property of the GPU that runs it, not of the method).  One warm-up
- * launch, then `repeats` timed launches of (SMs x 8) blocks x 256 threads, each thread running
- * 8 independent chains x <- x a + b for `iters` iterations; *dfma_per_second = DFMAs per launch
- * / median CUDA-event time (one DFMA = 2 flops).  Allocates a small device buffer and a stream
+ * hardware, so this is a property of the GPU that runs it, not of the method).  Three shapes --
+ * 4, 8 and 16 independent chains x <- x a + b per thread, (SMs x 16, 8, 4) blocks of 256
+ * threads, `iters` iterations -- each one warm-up launch and `repeats` timed launches;
+ * *dfma_per_second = the fastest shape's DFMAs per launch / its median CUDA-event time (one
+ * DFMA = 2 flops).  Allocates a small device buffer and a stream
  * for the call and frees them; synchronises.  iters in [1, 2^20], repeats in [1, 100], else
  * LBMHD_ERR_INVALID; CUDA failures return LBMHD_ERR_CUDA (message: lbmhd_last_error(NULL)). */
 int lbmhd_probe_fp64_fma_rate(int iters, int repeats, double* dfma_per_second);

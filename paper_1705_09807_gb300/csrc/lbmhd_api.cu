@@ -63,10 +63,12 @@ int check_params(const lbmhd_params* p) {
     return fail(nullptr, LBMHD_ERR_INVALID, "grid %d x %d: both sides must be >= 3", p->nx, p->ny);
   if ((long long)p->nx * p->ny > (1LL << 31))
     return fail(nullptr, LBMHD_ERR_INVALID, "grid %d x %d exceeds 2^31 cells", p->nx, p->ny);
-  // the row stride (all 27 planes of one row, ghost and pad columns included) is an int
-  if ((long long)kQ * (((long long)p->nx + kXOff + 2 + 31) / 32 * 32) > INT_MAX)
-    return fail(nullptr, LBMHD_ERR_INVALID, "grid width %d too large: a row of all 27 planes must "
-                "hold fewer than 2^31 elements", p->nx);
+  // the row stride (all 27 planes of one row -- 29 for LBMHD_FP16_REL -- ghost and pad columns
+  // included) is an int
+  const int planes = p->precision == LBMHD_FP16_REL ? kQRel : kQ;
+  if ((long long)planes * (((long long)p->nx + kXOff + 2 + 31) / 32 * 32) > INT_MAX)
+    return fail(nullptr, LBMHD_ERR_INVALID, "grid width %d too large: a row of all %d planes must "
+                "hold fewer than 2^31 elements", p->nx, planes);
   for (int j = 3; j < 9; ++j)
     if (!(p->s[j] > 0.0 && p->s[j] < 2.0))
       return fail(nullptr, LBMHD_ERR_INVALID, "s[%d] = %g outside (0, 2)", j, p->s[j]);
@@ -74,7 +76,8 @@ int check_params(const lbmhd_params* p) {
     return fail(nullptr, LBMHD_ERR_INVALID, "s_m = %g outside (0, 2)", p->s_m);
   if (!(p->delta >= 0.0) || !std::isfinite(p->delta))
     return fail(nullptr, LBMHD_ERR_INVALID, "delta = %g must be finite and >= 0", p->delta);
-  if (p->precision != LBMHD_FP64 && p->precision != LBMHD_FP32 && p->precision != LBMHD_FP16)
+  if (p->precision != LBMHD_FP64 && p->precision != LBMHD_FP32 && p->precision != LBMHD_FP16 &&
+      p->precision != LBMHD_FP16_REL)
     return fail(nullptr, LBMHD_ERR_INVALID, "unknown precision %d", p->precision);
   if (p->grad_stencil != LBMHD_GRAD_CENTRAL && p->grad_stencil != LBMHD_GRAD_ISOTROPIC)
     return fail(nullptr, LBMHD_ERR_INVALID, "unknown grad_stencil %d", p->grad_stencil);
@@ -130,15 +133,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 3-D map {columns, 27 planes, ny rows} over one population copy, boxes of {box_width, 9, 1}
-// (one row of one 9-plane group: the strip plus box_lead columns on each side).
-int make_tensor_map(lbmhd_t* h, void* base, CUtensorMap* map) {
+// 3-D map {columns, 27 planes (29 for LBMHD_FP16_REL), ny rows} over one population copy,
+// boxes of {box_width, box_planes, 1}: one row of one 9-plane group (the strip plus box_lead
+// columns on each side), or of the two velocity-reference planes of the relative form.
+int make_tensor_map(lbmhd_t* h, void* base, CUtensorMap* map, int box_planes = 9) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return fail(nullptr, LBMHD_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   const cuuint64_t e = h->elem;
-  cuuint64_t dims[3] = {(cuuint64_t)h->geom.plane, (cuuint64_t)kQ, (cuuint64_t)h->geom.ny};
+  cuuint64_t dims[3] = {(cuuint64_t)h->geom.plane, (cuuint64_t)h->nplanes, (cuuint64_t)h->geom.ny};
   cuuint64_t strides[2] = {(cuuint64_t)h->geom.plane * e, (cuuint64_t)h->geom.pitch * e};
-  cuuint32_t box[3] = {(cuuint32_t)box_width((int)e), 9, 1};
+  cuuint32_t box[3] = {(cuuint32_t)box_width((int)e), (cuuint32_t)box_planes, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   const CUtensorMapDataType dt = e == 8   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                  : e == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -174,6 +178,7 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
   h->p = *p;
   h->precision = p->precision;
   h->elem = p->precision == LBMHD_FP64 ? 8 : (p->precision == LBMHD_FP32 ? 4 : 2);
+  h->nplanes = p->precision == LBMHD_FP16_REL ? kQRel : kQ;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) {
     delete h;
@@ -185,7 +190,7 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
   g.nx = p->nx;
   g.ny = p->ny;
   g.plane = (p->nx + kXOff + 2 + 31) / 32 * 32;  // one row of one plane
-  g.pitch = (int)(kQ * g.plane);                  // one row of all 27 planes
+  g.pitch = (int)(h->nplanes * g.plane);          // one row of all 27 (29) planes
   g.band = step_band_rows(p->nx, p->ny, p->precision, sms);
   // rates scaled by the diagonal of T T^T = (9, 6, 6, 4, 4, 12, 12, 180, 20) (Eq. FluidTMatrix)
   const double norm[9] = {9, 6, 6, 4, 4, 12, 12, 180, 20};
@@ -222,6 +227,7 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
   LB_INIT(prepare_step_kernels());
   for (int i = 0; i < 2; ++i) {
     int rc_map = make_tensor_map(h, h->pops[i], &h->tmap[i]);
+    if (!rc_map && h->precision == LBMHD_FP16_REL) rc_map = make_tensor_map(h, h->pops[i], &h->umap[i], 2);
     if (rc_map) {
       free_all(h);
       return rc_map;
@@ -248,9 +254,12 @@ cudaError_t launch_one(lbmhd_t* h, int from, int to, const float* corr = nullptr
     case LBMHD_FP32:
       return launch_step_f32(h->tmap[from], (float*)h->pops[to], h->geom, h->coef,
                              h->p.grad_stencil, h->err_flag, corr, from, h->stream);
-    default:
+    case LBMHD_FP16:
       return launch_step_f16(h->tmap[from], (__half*)h->pops[to], h->geom, h->coef,
                              h->p.grad_stencil, h->err_flag, corr, 0, h->stream);
+    default:  // LBMHD_FP16_REL (no correction: refused when it is attached)
+      return launch_step_f16rel(h->tmap[from], h->umap[from], (__half*)h->pops[to], h->geom, h->coef,
+                                h->p.grad_stencil, h->err_flag, h->stream);
   }
 }
 
@@ -539,7 +548,7 @@ int lbmhd_test_skip_row_copy(lbmhd_t* h, int enable) {
 
 int lbmhd_set_correction_device(lbmhd_t* h, const float* corr) {
   if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
-  if (corr && h->precision == LBMHD_FP16)
+  if (corr && (h->precision == LBMHD_FP16 || h->precision == LBMHD_FP16_REL))
     return fail(h, LBMHD_ERR_INVALID, "the subgrid correction needs binary64 or binary32 storage");
   if (corr && h->closure) return fail(h, LBMHD_ERR_INVALID, "detach the learned closure first");
   h->corr_static = corr;
@@ -550,7 +559,7 @@ int lbmhd_set_correction_device(lbmhd_t* h, const float* corr) {
 int lbmhd_set_closure(lbmhd_t* h, lbmhd_closure_t* c) {
   if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
   if (c) {
-    if (h->precision == LBMHD_FP16)
+    if (h->precision == LBMHD_FP16 || h->precision == LBMHD_FP16_REL)
       return fail(h, LBMHD_ERR_INVALID, "the learned closure needs binary64 or binary32 storage");
     if (h->p.nx != h->p.ny) return fail(h, LBMHD_ERR_INVALID, "the learned closure needs a square grid");
     if (h->corr_static) return fail(h, LBMHD_ERR_INVALID, "detach the static correction first");

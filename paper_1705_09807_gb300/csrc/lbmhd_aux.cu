@@ -14,13 +14,31 @@ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >
 // Stored (post-collision) populations whose pull gives the equilibria of the fields:
 // stored f*_i(x) = f_i^eq(fields(x + c_i)), so that f_i(x) = f*_i(x - c_i) = f_i^eq(x).
 // Eq. feq, written as the deviation f_i^eq - w_i; Eq. geq.  Ghost columns written too.
-template <typename T>
+// REL (relative binary16 storage, LBMHD_FP16_REL): the cell's velocity reference U is its own
+// initial u rounded to binary16 (planes kQ, kQ + 1), and each stored f value is taken relative
+// to w_i (1 + 3 c_i . U).
+template <typename T, bool REL = false>
 __global__ void init_eq_kernel(T* __restrict__ pops, StepGeom g, const double* __restrict__ rho,
                                const double* __restrict__ ux, const double* __restrict__ uy,
                                const double* __restrict__ bx, const double* __restrict__ by) {
   const long n = (long)g.nx * g.ny;
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
     const int x = (int)(c % g.nx), y = (int)(c / g.nx);
+    double Ux = 0.0, Uy = 0.0;
+    if constexpr (REL) {
+      const __half hx = __double2half(ux[c]), hy = __double2half(uy[c]);
+      Ux = (double)__half2float(hx);
+      Uy = (double)__half2float(hy);
+      const size_t o = (size_t)y * g.pitch + kXOff + x;
+      const T u2[2] = {hx, hy};
+#pragma unroll
+      for (int comp = 0; comp < 2; ++comp) {
+        T* pl = pops + (size_t)(kQ + comp) * g.plane + o;
+        pl[0] = u2[comp];
+        if (x < 2) pl[g.nx] = u2[comp];
+        if (x >= g.nx - 2) pl[-g.nx] = u2[comp];
+      }
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const long s = (long)wrapi(y + vy(i), g.ny) * g.nx + wrapi(x + vx(i), g.nx);
@@ -29,8 +47,9 @@ __global__ void init_eq_kernel(T* __restrict__ pops, StepGeom g, const double* _
       const double cb = vx(i) * b + vy(i) * d;
       const double csq = (double)(vx(i) * vx(i) + vy(i) * vy(i));
       const double w = wt(i);
-      const double fdev = w * (r - 1.0) + w * r * (3.0 * cu + 4.5 * cu * cu - 1.5 * (u * u + v * v)) +
-                          4.5 * w * (0.5 * (b * b + d * d) * csq - cb * cb);
+      double fdev = w * (r - 1.0) + w * r * (3.0 * cu + 4.5 * cu * cu - 1.5 * (u * u + v * v)) +
+                    4.5 * w * (0.5 * (b * b + d * d) * csq - cb * cb);
+      if (REL) fdev -= 3.0 * w * (vx(i) * Ux + vy(i) * Uy);
       const double gx = w * (b + 3.0 * (cu * b - cb * u));
       const double gy = w * (d + 3.0 * (cu * d - cb * v));
       const size_t o = (size_t)y * g.pitch + kXOff + x;
@@ -46,19 +65,26 @@ __global__ void init_eq_kernel(T* __restrict__ pops, StepGeom g, const double* _
   }
 }
 
-// Pull the 27 current populations of cell (x, y) in binary64, f as deviations.
-template <typename T>
+// Pull the 27 current populations of cell (x, y) in binary64, f as deviations (for REL, each f
+// value plus 3 w_i c_i . U of the source cell that stored it).
+template <typename T, bool REL = false>
 __device__ __forceinline__ void pull_cell(const T* __restrict__ pops, const StepGeom& g, int x,
                                           int y, double v[27]) {
 #pragma unroll
   for (int q = 0; q < 27; ++q) {
     const int i = q % 9;
     const int sx = wrapi(x - vx(i), g.nx), sy = wrapi(y - vy(i), g.ny);
-    v[q] = load_as<double>(pops[(size_t)plane_of(q) * g.plane + (size_t)sy * g.pitch + kXOff + sx]);
+    const size_t src = (size_t)sy * g.pitch + kXOff + sx;
+    v[q] = load_as<double>(pops[(size_t)plane_of(q) * g.plane + src]);
+    if (REL && q >= 1 && q < 9) {
+      const double Ux = load_as<double>(pops[(size_t)kQ * g.plane + src]);
+      const double Uy = load_as<double>(pops[(size_t)(kQ + 1) * g.plane + src]);
+      v[q] += 3.0 * wt(i) * (vx(i) * Ux + vy(i) * Uy);
+    }
   }
 }
 
-template <typename T>
+template <typename T, bool REL = false>
 __global__ void moments_kernel(const T* __restrict__ pops, StepGeom g, double* __restrict__ rho,
                                double* __restrict__ ux, double* __restrict__ uy,
                                double* __restrict__ bx, double* __restrict__ by) {
@@ -66,7 +92,7 @@ __global__ void moments_kernel(const T* __restrict__ pops, StepGeom g, double* _
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
     const int x = (int)(c % g.nx), y = (int)(c / g.nx);
     double v[27];
-    pull_cell(pops, g, x, y, v);
+    pull_cell<T, REL>(pops, g, x, y, v);
     double r = 0, jx = 0, jy = 0, sbx = 0, sby = 0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -85,13 +111,13 @@ __global__ void moments_kernel(const T* __restrict__ pops, StepGeom g, double* _
   }
 }
 
-template <typename T>
+template <typename T, bool REL = false>
 __global__ void populations_kernel(const T* __restrict__ pops, StepGeom g, double* __restrict__ out) {
   const long n = (long)g.nx * g.ny;
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
     const int x = (int)(c % g.nx), y = (int)(c / g.nx);
     double v[27];
-    pull_cell(pops, g, x, y, v);
+    pull_cell<T, REL>(pops, g, x, y, v);
 #pragma unroll
     for (int q = 0; q < 27; ++q) out[(size_t)q * n + c] = q < 9 ? v[q] + wt(q) : v[q];
   }
@@ -193,8 +219,10 @@ cudaError_t launch_init_eq(int precision, void* pops, const StepGeom& g, const d
     init_eq_kernel<double><<<grid, 256, 0, s>>>((double*)pops, g, rho, ux, uy, bx, by);
   else if (precision == 1)
     init_eq_kernel<float><<<grid, 256, 0, s>>>((float*)pops, g, rho, ux, uy, bx, by);
-  else
+  else if (precision == LBMHD_FP16)
     init_eq_kernel<__half><<<grid, 256, 0, s>>>((__half*)pops, g, rho, ux, uy, bx, by);
+  else
+    init_eq_kernel<__half, true><<<grid, 256, 0, s>>>((__half*)pops, g, rho, ux, uy, bx, by);
   return cudaGetLastError();
 }
 
@@ -205,8 +233,10 @@ cudaError_t launch_moments(int precision, const void* pops, const StepGeom& g, d
     moments_kernel<double><<<grid, 256, 0, s>>>((const double*)pops, g, rho, ux, uy, bx, by);
   else if (precision == 1)
     moments_kernel<float><<<grid, 256, 0, s>>>((const float*)pops, g, rho, ux, uy, bx, by);
-  else
+  else if (precision == LBMHD_FP16)
     moments_kernel<__half><<<grid, 256, 0, s>>>((const __half*)pops, g, rho, ux, uy, bx, by);
+  else
+    moments_kernel<__half, true><<<grid, 256, 0, s>>>((const __half*)pops, g, rho, ux, uy, bx, by);
   return cudaGetLastError();
 }
 
@@ -217,8 +247,10 @@ cudaError_t launch_populations(int precision, const void* pops, const StepGeom& 
     populations_kernel<double><<<grid, 256, 0, s>>>((const double*)pops, g, out);
   else if (precision == 1)
     populations_kernel<float><<<grid, 256, 0, s>>>((const float*)pops, g, out);
-  else
+  else if (precision == LBMHD_FP16)
     populations_kernel<__half><<<grid, 256, 0, s>>>((const __half*)pops, g, out);
+  else
+    populations_kernel<__half, true><<<grid, 256, 0, s>>>((const __half*)pops, g, out);
   return cudaGetLastError();
 }
 

@@ -224,6 +224,8 @@ int lbmhd_ensemble_create(lbmhd_ensemble_t** out, int n, const lbmhd_params* par
   for (int i = 0; i < n; ++i) {
     if (params[i].precision != params[0].precision || params[i].grad_stencil != params[0].grad_stencil)
       return efail(nullptr, LBMHD_ERR_INVALID, "members must share precision and gradient stencil");
+    if (params[i].precision == LBMHD_FP16_REL)
+      return efail(nullptr, LBMHD_ERR_INVALID, "ensembles take LBMHD_FP64, LBMHD_FP32 or LBMHD_FP16 members");
     for (int k = 0; k < 5; ++k)
       if (!fields[5 * i + k]) return efail(nullptr, LBMHD_ERR_INVALID, "member %d: field pointer NULL", i);
   }

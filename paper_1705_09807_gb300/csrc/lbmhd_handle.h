@@ -17,6 +17,8 @@ struct lbmhd {
   lbmhd_gpu::StepGeom geom{};
   lbmhd_gpu::StepCoef coef{};
   size_t elem = 8;         // bytes per stored population value
+  int nplanes = 27;        // planes per row: 27 populations (+ 2 velocity-reference planes for
+                           // LBMHD_FP16_REL)
   size_t state_bytes = 0;  // one population copy
   void* pops[2] = {nullptr, nullptr};
   int cur = 0;             // copy holding the current state
@@ -29,6 +31,7 @@ struct lbmhd {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   long graph_launches = 0;  // kernel launches in one captured graph
   CUtensorMap tmap[2];             // 3-D TMA descriptors of the two copies
+  CUtensorMap umap[2];             // LBMHD_FP16_REL: the same copies, boxes over the U planes
   unsigned* err_flag = nullptr;    // device word: set by the step kernel on a pipeline timeout
   void* spec_work = nullptr;       // spectrum work buffer and outputs (allocated on first use)
   const float* corr_static = nullptr;    // caller's correction planes [4][ny][nx] (not owned)

@@ -113,6 +113,12 @@ cudaError_t launch_step_f32(const CUtensorMap& src, float* dst, const StepGeom& 
 cudaError_t launch_step_f16(const CUtensorMap& src, __half* dst, const StepGeom& g,
                             const StepCoef& c, int stencil, unsigned* err, const float* corr,
                             int flip, cudaStream_t s);
+// Relative binary16 storage (LBMHD_FP16_REL): the 27 planes hold f_i - w_i (1 + 3 c_i . U) and g_i,
+// and two more planes per row (kQ, kQ + 1) the velocity reference U_x, U_y of the cell that wrote
+// them (binary16); usrc is a tensor map over the same copy with boxes {box_width(2), 2, 1}.
+constexpr int kQRel = kQ + 2;
+cudaError_t launch_step_f16rel(const CUtensorMap& src, const CUtensorMap& usrc, __half* dst, const StepGeom& g,
+                               const StepCoef& c, int stencil, unsigned* err, cudaStream_t s);
 // Rows per block for the grid and precision (one wave of resident blocks when possible).
 int step_band_rows(int nx, int ny, int precision, int num_sms);
 // Opt the step kernels in to their dynamic shared memory (once per process and device).
@@ -134,7 +140,8 @@ cudaError_t launch_ensemble_step(int precision, int stencil, const void* members
                                  unsigned* err, cudaStream_t s);
 int resident_step_blocks(int precision, int num_sms);
 
-// Auxiliary kernels (lbmhd_aux.cu).  `precision` selects double / float / half storage.
+// Auxiliary kernels (lbmhd_aux.cu).  `precision` selects double / float / half storage (and the
+// relative binary16 form, LBMHD_FP16_REL).
 cudaError_t launch_init_eq(int precision, void* pops, const StepGeom& g, const double* rho,
                            const double* ux, const double* uy, const double* bx, const double* by,
                            cudaStream_t s);

@@ -212,10 +212,11 @@ __device__ __forceinline__ KCoef2 pair_coef(const KCoef<float>& c) {
 // `collide` for two cells at once (same equations and operation order per lane, with the
 // products that the scalar form leaves to the compiler's contraction written as fma).
 __device__ __forceinline__ void collide_pair(F2 p[kQ], F2 rho1, F2 jx, F2 jy, F2 bx, F2 by, const F2 dJ[4],
-                                             const F2 dB[4], const KCoef2& c) {
+                                             const F2 dB[4], const KCoef2& c, F2* ir_out = nullptr) {
   const F2 one = f2(1.f), two = f2(2.f), three = f2(3.f), four = f2(4.f), five = f2(5.f);
   const F2 r = one + rho1;
   const F2 ir = f2(1.f / lo(r), 1.f / hi(r));
+  if (ir_out) *ir_out = ir;
   const F2 k = c.kq;
   const F2 Gxx = fma2(dJ[1], dJ[1], dJ[0] * dJ[0]);
   const F2 Gyy = fma2(dJ[3], dJ[3], dJ[2] * dJ[2]);
@@ -291,10 +292,28 @@ __device__ __forceinline__ void collide_pair(F2 p[kQ], F2 rho1, F2 jx, F2 jy, F2
 template <typename S> struct ArithOf { using type = S; };
 template <> struct ArithOf<__half> { using type = float; };
 
-// Shared memory of one block: NST row stages, the moment ring, the stage barriers.
-template <typename S, int NST>
-struct StepSmem {
+// Binary16 storage relative to the local velocity (LBMHD_FP16_REL): the velocity references
+// U_x, U_y of kURing staged source rows ([row][component][box column]), indexed by march index.
+// Rows in use at once: the collision of row m reads m-1 .. m+1, the moments of row m+1 read
+// m .. m+2, and the copy issued in the same iteration brings m+3 (NST = 3): five, so six slots.
+// Each ring row is the destination of one tensor copy ({BW columns, 2 planes}: U_x at [0, BW),
+// U_y at [BW, 2 BW)), which must start on a 128-byte boundary in shared memory, so rows are
+// padded to a multiple of 128 bytes (576 -> 640 B at BW = 144).
+constexpr int kURing = 6;
+__host__ __device__ constexpr int urow_elems(int bw) { return (2 * bw * 2 + 127) / 128 * 128 / 2; }
+template <bool REL, int BW> struct URingSmem {};
+template <int BW> struct URingSmem<true, BW> {
+  static_assert(urow_elems(BW) * 2 % 128 == 0 && urow_elems(BW) >= 2 * BW, "U rows on 128-byte boundaries");
+  __half uring[kURing][urow_elems(BW)];  // 3840 B at BW = 144
+};
+
+// Shared memory of one block: NST row stages, the moment ring, the stage barriers (and, for the
+// relative binary16 form, the U ring, first: 3840 B, a multiple of 128, so the stages stay
+// 128-byte aligned).
+template <typename S, int NST, bool REL = false>
+struct StepSmem : URingSmem<REL, box_width((int)sizeof(S))> {
   using C = typename ArithOf<S>::type;
+  static constexpr int kNst = NST;
   static constexpr int kLead = box_lead((int)sizeof(S));
   static constexpr int kBoxW = box_width((int)sizeof(S));
   static constexpr int kGroupElems = ((9 * kBoxW * (int)sizeof(S) + 127) / 128 * 128) / (int)sizeof(S);
@@ -345,18 +364,20 @@ __device__ __forceinline__ void moments_from(const S* st, int ge, int col, C& rh
 }
 
 // Dynamic shared memory of a step block, rounded up to the 128-byte alignment TMA needs.
-template <typename S, int NST>
-__device__ __forceinline__ StepSmem<S, NST>& step_smem() {
+template <typename S, int NST, bool REL = false>
+__device__ __forceinline__ StepSmem<S, NST, REL>& step_smem() {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  return *reinterpret_cast<StepSmem<S, NST>*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+  return *reinterpret_cast<StepSmem<S, NST, REL>*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
 }
 
-template <typename S, int NST>
-__device__ __forceinline__ void init_stage_barriers(StepSmem<S, NST>& S_, const CUtensorMap* prefetch) {
+template <typename SM>
+__device__ __forceinline__ void init_stage_barriers(SM& S_, const CUtensorMap* prefetch,
+                                                    const CUtensorMap* prefetch2 = nullptr) {
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NST; ++s) mbar_init(&S_.full[s], 1);
+    for (int s = 0; s < SM::kNst; ++s) mbar_init(&S_.full[s], 1);
     fence_barrier_init();
     if (prefetch) prefetch_tmap(prefetch);
+    if (prefetch2) prefetch_tmap(prefetch2);
   }
 }
 
@@ -587,10 +608,68 @@ __device__ __forceinline__ F2 staged_pair(const __half* st, int ge, int q, int c
   return f2(__half2float(a[0]), __half2float(a[1]));
 }
 
+// Relative binary16 storage (LBMHD_FP16_REL): stored f values are s_i = f*_i - w_i (1 + 3 c_i . U)
+// with U the velocity reference of the cell that wrote them (planes 27, 28); the deviation f_i - w_i
+// of a pulled population is s_i + 3 w_i c_i . U(source cell).  urow[g] is the staged U row
+// ([2][BW]: U_x, then U_y) of the source row of plane group g.
 template <int BW>
+__device__ __forceinline__ F2 u_pair(const __half* ur, int comp, int c) {  // U_comp at columns c, c + 1
+  const __half* a = ur + comp * BW + c;
+  if ((c & 1) == 0) {  // even column: one aligned 32-bit load
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(a));
+    return f2(v.x, v.y);
+  }
+  return f2(__half2float(a[0]), __half2float(a[1]));
+}
+__device__ __forceinline__ constexpr float w3_of(int i) { return i < 5 ? 1.f / 3.f : 1.f / 12.f; }  // 3 w_i
+
+template <int BW, bool REL>
+__device__ __forceinline__ F2 staged_pair_rel(const __half* st, int ge, int q, int col, const __half* const* urow) {
+  F2 v = staged_pair<BW>(st, ge, q, col);
+  if constexpr (REL) {
+    if (q >= 1 && q < 9) {
+      const int c = col - vel_x(q);
+      const __half* ur = urow[group_of(q)];
+      if (!LB_IN(c >= 0 && c + 1 < BW, 0)) return v;
+      if (vel_x(q) != 0) v = fma2(f2((float)vel_x(q) * w3_of(q)), u_pair<BW>(ur, 0, c), v);
+      if (vel_y(q) != 0) v = fma2(f2((float)vel_y(q) * w3_of(q)), u_pair<BW>(ur, 1, c), v);
+    }
+  }
+  return v;
+}
+
+// Scalar (one cell) pulled value for the relative form, as staged_pair_rel.
+template <int BW, bool REL>
+__device__ __forceinline__ float staged_rel(const __half* st, int ge, int q, int col, const __half* const* urow) {
+  float v = staged<float, __half, BW>(st, ge, q, col);
+  if constexpr (REL) {
+    if (q >= 1 && q < 9) {
+      const int c = col - vel_x(q);
+      const __half* ur = urow[group_of(q)];
+      if (!LB_IN(c >= 0 && c < BW, 0)) return v;
+      if (vel_x(q) != 0) v = fmaf((float)vel_x(q) * w3_of(q), __half2float(ur[c]), v);
+      if (vel_y(q) != 0) v = fmaf((float)vel_y(q) * w3_of(q), __half2float(ur[BW + c]), v);
+    }
+  }
+  return v;
+}
+
+template <int BW, bool REL>
+__device__ __forceinline__ void moments_one_rel(const __half* st, int ge, int col, const __half* const* urow,
+                                                float& rho1, float& jx, float& jy, float& bx, float& by) {
+  auto v = [&](int q) -> float { return staged_rel<BW, REL>(st, ge, q, col, urow); };
+  const float f0 = v(0), f1 = v(1), f2_ = v(2), f3 = v(3), f4 = v(4), f5 = v(5), f6 = v(6), f7 = v(7), f8 = v(8);
+  rho1 = ((f0 + f1) + (f2_ + f3)) + ((f4 + f5) + (f6 + f7)) + f8;
+  jx = (f1 - f3) + (f5 - f6) + (f8 - f7);
+  jy = (f2_ - f4) + (f5 - f8) + (f6 - f7);
+  bx = ((v(9) + v(10)) + (v(11) + v(12))) + ((v(13) + v(14)) + (v(15) + v(16))) + v(17);
+  by = ((v(18) + v(19)) + (v(20) + v(21))) + ((v(22) + v(23)) + (v(24) + v(25))) + v(26);
+}
+
+template <int BW, bool REL = false>
 __device__ __forceinline__ void moments_pair(const __half* st, int ge, int col, F2& rho1, F2& jx, F2& jy, F2& bx,
-                                             F2& by) {
-  auto v = [&](int q) -> F2 { return staged_pair<BW>(st, ge, q, col); };
+                                             F2& by, const __half* const* urow = nullptr) {
+  auto v = [&](int q) -> F2 { return staged_pair_rel<BW, REL>(st, ge, q, col, urow); };
   const F2 f0 = v(0), f1 = v(1), f2_ = v(2), f3 = v(3), f4 = v(4), f5 = v(5), f6 = v(6), f7 = v(7), f8 = v(8);
   rho1 = ((f0 + f1) + (f2_ + f3)) + ((f4 + f5) + (f6 + f7)) + f8;
   jx = (f1 - f3) + (f5 - f6) + (f8 - f7);
@@ -619,17 +698,24 @@ __device__ __forceinline__ void store_planes_pair(__half* op, const F2* p, size_
 // One tile of a binary16 grid with two adjacent cells per thread (kStepThreads / 2 threads per
 // strip of kStepThreads columns): the pipeline of run_tile, with the moments, the collision
 // and the stores of a cell pair in packed binary32 (F2).  Same arguments and contract as run_tile.
-template <int ISO, int NST>
+// REL: relative binary16 storage (LBMHD_FP16_REL, single-grid steps only): usrcp maps the U
+// planes (27, 28: U_x, U_y of the writing cell, boxes {BW, 2, 1}); each staged row also brings the
+// U row of the source row one ahead in march order (the first also the two before it) into the U
+// ring, the pulled f values are taken relative to their source cells' U (staged_pair_rel), and
+// the post-collision f values are stored relative to this cell's own velocity, which is stored
+// in binary16 as its U.
+template <int ISO, int NST, bool REL = false>
 __device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* __restrict__ dst, const StepGeom& g,
                                               const KCoef<float>& c1, int x0, int y0, int band_parity,
-                                              uint32_t& kbase, unsigned* __restrict__ err) {
-  using SM = StepSmem<__half, NST>;
+                                              uint32_t& kbase, unsigned* __restrict__ err,
+                                              const CUtensorMap* usrcp = nullptr) {
+  using SM = StepSmem<__half, NST, REL>;
   constexpr int GE = SM::kGroupElems;
   constexpr int LEAD = SM::kLead;
   constexpr int BW = SM::kBoxW;
   constexpr int RW = SM::kRingW;
   static_assert(SM::kRingOff == 2, "pair layout");
-  SM& S_ = step_smem<__half, NST>();
+  SM& S_ = step_smem<__half, NST, REL>();
 
   const int t = threadIdx.x;
   const int c0 = 2 * t;  // first of this thread's two strip columns
@@ -659,9 +745,26 @@ __device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* _
     const int rc = r == ny - 1 ? 0 : r + 1;
     const int cx = x0 + kXOff - LEAD;
     const bool in = LB_IN(ra >= 0 && ra < ny && r >= 0 && r < ny && rc >= 0 && rc < ny && cx >= 0, 3);
-    mbar_arrive_expect_tx(&S_.full[s], in ? SM::kTxBytes : 0u);  // 0: the phase completes empty
+    constexpr uint32_t kUBytes = 2u * BW * 2u;  // one U row
+    const uint32_t ubytes = REL ? (k == 0 ? 3u : 1u) * kUBytes : 0u;
+    mbar_arrive_expect_tx(&S_.full[s], in ? SM::kTxBytes + ubytes : 0u);  // 0: the phase completes empty
     if (in) {
       copy_row_boxes(S_.stage[s], GE, srcp, cx, ra, r, rc, &S_.full[s], k < 2);
+      if constexpr (REL) {  // U rows of march indices k + 1 (and k - 1, k for the first row)
+        for (int j = (k == 0 ? -1 : k + 1); j <= k + 1; ++j)
+          tma_load_3d(&S_.uring[(j + kURing) % kURing][0], usrcp, cx, kQ, row_of(j), &S_.full[s]);
+      }
+    }
+  };
+  // staged U rows of the source rows of the three plane groups of march row k (groups 0, 1, 2
+  // are pulled from rows y - 1, y, y + 1: march indices k - dir, k, k + dir)
+  auto urows = [&](int k, const __half* (&u)[3]) {
+    if constexpr (REL) {
+      u[0] = &S_.uring[(k - dir + kURing) % kURing][0];
+      u[1] = &S_.uring[(k + kURing) % kURing][0];
+      u[2] = &S_.uring[(k + dir + kURing) % kURing][0];
+    } else {
+      u[0] = u[1] = u[2] = nullptr;
     }
   };
   auto slot = [&](int k) -> int { return (int)((kb + (uint32_t)k) % NST); };
@@ -676,9 +779,11 @@ __device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* _
   auto ring_moments = [&](int k) {
     const __half* st = S_.stage[slot(k)];
     float* rg = &S_.ring[k & (kRing - 1)][0][0];
+    const __half* ur[3];
+    urows(k, ur);
     if (active) {
       F2 r1, jx, jy, bx, by;
-      moments_pair<BW>(st, GE, c0 + LEAD, r1, jx, jy, bx, by);
+      moments_pair<BW, REL>(st, GE, c0 + LEAD, r1, jx, jy, bx, by, ur);
       *reinterpret_cast<uint64_t*>(rg + 0 * RW + c0 + 2) = jx.v;
       *reinterpret_cast<uint64_t*>(rg + 1 * RW + c0 + 2) = jy.v;
       *reinterpret_cast<uint64_t*>(rg + 2 * RW + c0 + 2) = bx.v;
@@ -687,14 +792,14 @@ __device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* _
     }
     float r1, jx, jy, bx, by;
     if (t == 0) {
-      moments_from<float, __half, BW>(st, GE, LEAD - 1, r1, jx, jy, bx, by);
+      moments_one_rel<BW, REL>(st, GE, LEAD - 1, ur, r1, jx, jy, bx, by);
       rg[0 * RW + 1] = jx;
       rg[1 * RW + 1] = jy;
       rg[2 * RW + 1] = bx;
       rg[3 * RW + 1] = by;
     }
     if (t == last && (ncol & 1) == 0) {
-      moments_from<float, __half, BW>(st, GE, ncol + LEAD, r1, jx, jy, bx, by);
+      moments_one_rel<BW, REL>(st, GE, ncol + LEAD, ur, r1, jx, jy, bx, by);
       rg[0 * RW + ncol + 2] = jx;
       rg[1 * RW + ncol + 2] = jy;
       rg[2 * RW + ncol + 2] = bx;
@@ -775,15 +880,50 @@ __device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* _
         }
       }
       const __half* st = S_.stage[slot(m)];
+      const __half* ur[3];
+      urows(m, ur);
       F2 p[kQ];
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) p[q] = staged_pair<BW>(st, GE, q, c0 + LEAD);
-      collide_pair(p, rho_cur, own[0], own[1], own[2], own[3], dJ, dB, c);
+      for (int q = 0; q < kQ; ++q) p[q] = staged_pair_rel<BW, REL>(st, GE, q, c0 + LEAD, ur);
+      F2 ir;
+      collide_pair(p, rho_cur, own[0], own[1], own[2], own[3], dJ, dB, c, &ir);
       const int y = row_of(m);
       const int x = x0 + c0;
       __half* o = dst + (size_t)y * pitch + kXOff + x;
       const __half* end = dst + (size_t)g.pitch * ny;  // one past the copy (checking build)
+      __half2 uh[2];  // this cell pair's velocity reference U_x, U_y (binary16)
+      if constexpr (REL) {
+        // u = J / rho of the cells (collision invariants), rounded to binary16; the f values are
+        // stored relative to w_i (1 + 3 c_i . U): f_1 -= U_x / 3, f_3 += U_x / 3, f_2 -= U_y / 3,
+        // f_4 += U_y / 3, f_5 -= (U_x + U_y) / 12, f_7 += (U_x + U_y) / 12, f_6 -= (U_y - U_x) / 12,
+        // f_8 += (U_y - U_x) / 12
+        const F2 ux = own[0] * ir, uy = own[1] * ir;
+        uh[0] = __floats2half2_rn(lo(ux), hi(ux));
+        uh[1] = __floats2half2_rn(lo(uy), hi(uy));
+        const float2 fx = __half22float2(uh[0]), fy = __half22float2(uh[1]);
+        const F2 Ux = f2(fx.x, fx.y), Uy = f2(fy.x, fy.y);
+        const F2 a = f2(1.f / 3.f) * Ux, b = f2(1.f / 3.f) * Uy;
+        const F2 d1 = f2(1.f / 12.f) * (Ux + Uy), d2 = f2(1.f / 12.f) * (Uy - Ux);
+        p[1] = p[1] - a;
+        p[3] = p[3] + a;
+        p[2] = p[2] - b;
+        p[4] = p[4] + b;
+        p[5] = p[5] - d1;
+        p[7] = p[7] + d1;
+        p[6] = p[6] - d2;
+        p[8] = p[8] + d2;
+      }
       store_planes_pair<0>(o, p, g.plane, c0 + 1 < ncol, dst, end);
+      if constexpr (REL) {
+#pragma unroll
+        for (int comp = 0; comp < 2; ++comp) {
+          __half* a = o + (size_t)(kQ + comp) * g.plane;
+          if (LB_IN(a >= dst && a + (c0 + 1 < ncol ? 2 : 1) <= end, 2)) {
+            if (c0 + 1 < ncol) *reinterpret_cast<__half2*>(a) = uh[comp];
+            else *a = __low2half(uh[comp]);
+          }
+        }
+      }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int xh = x + h;
@@ -794,6 +934,13 @@ __device__ __forceinline__ bool run_tile_pair(const CUtensorMap* srcp, __half* _
           for (int q = 0; q < kQ; ++q) {
             __half* a = gp + (size_t)plane_of(q) * g.plane;
             if (LB_IN(a >= dst && a < end, 2)) *a = __float2half_rn(h ? hi(p[q]) : lo(p[q]));
+          }
+          if constexpr (REL) {
+#pragma unroll
+            for (int comp = 0; comp < 2; ++comp) {
+              __half* a = gp + (size_t)(kQ + comp) * g.plane;
+              if (LB_IN(a >= dst && a < end, 2)) *a = h ? __high2half(uh[comp]) : __low2half(uh[comp]);
+            }
           }
         }
       }
@@ -838,6 +985,20 @@ __global__ void __launch_bounds__(step_threads<S>(), MINB)
   uint32_t kbase = 0;
   run_any_tile<S, ISO, NST, CORR>(&src, dst, g, c, blockIdx.x * kStepThreads, blockIdx.y * g.band,
                                   (int)blockIdx.y + flip, kbase, err, corr);
+}
+
+// Relative binary16 storage (LBMHD_FP16_REL; single grids): fused_step_kernel's binary16 step
+// with the U planes' tensor map (fixed marching direction, as for binary16).
+template <int ISO, int NST, int MINB>
+__global__ void __launch_bounds__(kStepThreads / 2, MINB)
+    fused_step_rel_kernel(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap usrc,
+                          __half* __restrict__ dst, StepGeom g, KCoef<float> c, unsigned* __restrict__ err) {
+  if ((int)blockIdx.y * g.band >= g.ny) return;  // uniform per block
+  init_stage_barriers(step_smem<__half, NST, true>(), &src, &usrc);
+  grid_dependency_wait();
+  uint32_t kbase = 0;
+  run_tile_pair<ISO, NST, true>(&src, dst, g, c, blockIdx.x * kStepThreads, blockIdx.y * g.band, blockIdx.y, kbase,
+                                err, &usrc);
 }
 
 // Ensemble: every member grid advances one step in this launch.  work[i] = {member, x0, y0,
@@ -957,6 +1118,14 @@ constexpr size_t smem_bytes() {
   return sizeof(StepSmem<S, StepConfig<S>::kStages>) + 128;  // + alignment slack
 }
 
+template <int ISO>
+constexpr auto rel_kernel_ptr() {
+  return &fused_step_rel_kernel<ISO, StepConfig<__half>::kStages, StepConfig<__half>::kMinBlocks>;
+}
+constexpr size_t rel_smem_bytes() { return sizeof(StepSmem<__half, StepConfig<__half>::kStages, true>) + 128; }
+// six relative-form blocks per SM: 6 x (rel_smem_bytes + 1 KB reserved) within 228 KB
+static_assert(6 * (rel_smem_bytes() + 1024) <= 228 * 1024, "relative binary16 blocks fit six per SM");
+
 // Steps are launched with programmatic stream serialisation (launch_programmatic): a step's
 // blocks may be scheduled while the previous kernel in the stream drains and wait
 // (grid_dependency_wait) before touching global memory.  Measured: 6.5% less time per step at
@@ -980,6 +1149,16 @@ cudaError_t launch_step(const CUtensorMap& src, S* dst, const StepGeom& g, const
   const float* none = nullptr;
   return stencil == 1 ? launch_programmatic(kernel_ptr<S, 1>(), grid, nt, sm, s, src, dst, g, k, err, none, flip)
                       : launch_programmatic(kernel_ptr<S, 0>(), grid, nt, sm, s, src, dst, g, k, err, none, flip);
+}
+
+cudaError_t launch_step_rel(const CUtensorMap& src, const CUtensorMap& usrc, __half* dst, const StepGeom& g,
+                            const StepCoef& c, int stencil, unsigned* err, cudaStream_t s) {
+  dim3 grid((g.nx + kStepThreads - 1) / kStepThreads, (g.ny + g.band - 1) / g.band);
+  const KCoef<float> k = cast_coef<float>(c);
+  const int nt = kStepThreads / 2;
+  const size_t sm = rel_smem_bytes();
+  return stencil == 1 ? launch_programmatic(rel_kernel_ptr<1>(), grid, nt, sm, s, src, usrc, dst, g, k, err)
+                      : launch_programmatic(rel_kernel_ptr<0>(), grid, nt, sm, s, src, usrc, dst, g, k, err);
 }
 
 template <typename S, int ISO>
@@ -1053,6 +1232,10 @@ cudaError_t prepare_step_kernels() {
   cudaError_t e = set_smem_attr<float>();
   if (e == cudaSuccess) e = set_smem_attr<double>();
   if (e == cudaSuccess) e = set_smem_attr<__half>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(rel_kernel_ptr<0>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rel_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(rel_kernel_ptr<1>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rel_smem_bytes());
 #ifdef LBMHD_BOUNDS_CHECK
   const char* env = getenv("LBMHD_BOUNDS_FORCE");
   const unsigned force = env ? (unsigned)strtoul(env, nullptr, 0) : 0u;
@@ -1079,6 +1262,11 @@ cudaError_t launch_step_f16(const CUtensorMap& src, __half* dst, const StepGeom&
   return launch_step<__half>(src, dst, g, c, stencil, err, corr, flip, s);
 }
 
+cudaError_t launch_step_f16rel(const CUtensorMap& src, const CUtensorMap& usrc, __half* dst, const StepGeom& g,
+                               const StepCoef& c, int stencil, unsigned* err, cudaStream_t s) {
+  return launch_step_rel(src, usrc, dst, g, c, stencil, err, s);
+}
+
 size_t ensemble_member_bytes(int precision) {
   return precision == 0 ? sizeof(EnsembleMember<double>)
                         : (precision == 1 ? sizeof(EnsembleMember<float>) : sizeof(EnsembleMember<__half>));
@@ -1102,7 +1290,7 @@ cudaError_t launch_ensemble_step(int precision, int stencil, const void* members
 int resident_step_blocks(int precision, int num_sms) {
   const int per_sm = precision == 0   ? StepConfig<double>::kMinBlocks
                      : precision == 1 ? StepConfig<float>::kMinBlocks
-                                      : StepConfig<__half>::kMinBlocks;
+                                      : StepConfig<__half>::kMinBlocks;  // binary16, both forms
   return num_sms * per_sm;
 }
 
@@ -1113,7 +1301,7 @@ int step_band_rows(int nx, int ny, int precision, int num_sms) {
   const int strips = (nx + kStepThreads - 1) / kStepThreads;
   const int per_sm = precision == 0   ? StepConfig<double>::kMinBlocks
                      : precision == 1 ? StepConfig<float>::kMinBlocks
-                                      : StepConfig<__half>::kMinBlocks;
+                                      : StepConfig<__half>::kMinBlocks;  // binary16, both forms
   const long resident = (long)num_sms * per_sm * LBMHD_WAVES;
   long bands = resident / strips;
   if (bands < 1) bands = 1;

@@ -26,6 +26,7 @@ LBMHD_ERR_UNSTABLE = -4
 LBMHD_FP64 = 0
 LBMHD_FP32 = 1
 LBMHD_FP16 = 2
+LBMHD_FP16_REL = 3
 LBMHD_ERR_TIMEOUT = -5
 LBMHD_GRAD_CENTRAL = 0
 LBMHD_GRAD_ISOTROPIC = 1

@@ -113,3 +113,21 @@ def test_bounds_checking_variant_builds_and_exports_the_same_functions():
     chk = ctypes.CDLL(path)
     for n in lbmhd.header_functions():
         assert hasattr(chk, n), n
+
+
+def test_relative_binary16_form_host_checks(lib):
+    """LBMHD_FP16_REL stores two more planes per row, so its width limit is lower (a row of all
+    29 planes must stay below 2^31 elements), and ensembles refuse it; both are host checks."""
+    D = ctypes.POINTER(ctypes.c_double)
+    arrs = [np.ascontiguousarray(a) for a in _fields(8, 8)]
+    p = lbmhd.lbmhd_params_srt(8, 8, 0.01, 0.01, 1.0, lbmhd.LBMHD_FP16_REL)
+    p.nx, p.ny = 74_051_103, 3
+    h = ctypes.c_void_p()
+    rc = lib.lbmhd_init(ctypes.byref(h), ctypes.byref(p), *(a.ctypes.data_as(D) for a in arrs))
+    assert rc == lbmhd.LBMHD_ERR_INVALID and "29 planes" in lbmhd.lbmhd_last_error(None)
+    p = lbmhd.lbmhd_params_srt(8, 8, 0.01, 0.01, 1.0, lbmhd.LBMHD_FP16_REL)
+    fields = (D * 5)(*(a.ctypes.data_as(D) for a in arrs))
+    e = ctypes.c_void_p()
+    rc = lib.lbmhd_ensemble_create(ctypes.byref(e), 1, ctypes.byref(p), fields, None)
+    assert rc == lbmhd.LBMHD_ERR_INVALID and not e.value
+    assert "ensembles take" in lib.lbmhd_ensemble_last_error(None).decode()

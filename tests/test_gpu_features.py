@@ -25,7 +25,8 @@ def _params(n, precision=lbmhd.LBMHD_FP64, delta=2.0, stream=None, stencil=0):
     return lbmhd.make_params(n, n, s, sm, delta, precision, stencil, stream)
 
 
-@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32, lbmhd.LBMHD_FP16])
+@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32, lbmhd.LBMHD_FP16,
+                                       lbmhd.LBMHD_FP16_REL])
 def test_checkpoint_resume_bitwise(precision):
     fields = kh_jet(96, seed=4)
     with lbmhd.Lbmhd(_params(96, precision), *fields) as sim:
@@ -177,7 +178,8 @@ def test_argument_errors_on_a_live_handle():
         assert sim.launches == launches + 65 and sim.steps == 65
 
 
-@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32, lbmhd.LBMHD_FP16])
+@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32, lbmhd.LBMHD_FP16,
+                                       lbmhd.LBMHD_FP16_REL])
 def test_pipeline_wait_timeout_reported_and_context_usable(precision):
     """Failure detection without a fault: one block leaves out one staged-row copy, so its
     time-bounded mbarrier wait runs out; the step reports LBMHD_ERR_TIMEOUT to the host, the

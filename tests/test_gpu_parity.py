@@ -180,6 +180,49 @@ def test_fp16_kh_jet_64_against_fp64_oracle(steps):
         assert e[name] < tol, (name, e)
 
 
+# The relative binary16 form (LBMHD_FP16_REL) stores f_i - w_i (1 + 3 c_i . U), U the writing
+# cell's velocity in binary16, so the O(u) part of f_i (3 w_i c_i . u ~ 0.017 here) is not
+# rounded: rho - 1 is resolved (2.8% / 2.1% / 1.1% relative at steps 100 / 500 / 1000, against
+# 38% / 23% / 10% for binary16), u_x and u_y are 2-10x closer, B as binary16.  Bounds about 3x
+# the measured values (comments).
+FP16_REL_BOUNDS = {
+    #        rho - 1  u_x     u_y    B_x     B_y     (measured)
+    100: (0.08, 2e-4, 0.012, 2.4e-3, 0.023),     # 0.028 / 6.9e-5 / 4.2e-3 / 8.0e-4 / 7.7e-3
+    500: (0.06, 1.2e-3, 0.04, 4.2e-3, 0.07),     # 0.021 / 4.0e-4 / 0.0136 / 1.4e-3 / 0.023
+    1000: (0.032, 2.8e-3, 0.023, 6.8e-3, 0.035),  # 0.0106 / 9.2e-4 / 7.6e-3 / 2.3e-3 / 0.0118
+}
+
+
+@pytest.mark.parametrize("steps", [100, 500, 1000])
+def test_fp16_rel_kh_jet_64_against_fp64_oracle(steps):
+    """Relative binary16 storage against the FP64 oracle, each component on its own, and rho - 1
+    at least 4x closer than plain binary16 storage on the same run."""
+    n = 64
+    fields = kh_jet(n, seed=1)
+    s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
+    _, _, mom, omom = run_pair(fields, s, sm, 2.0, steps, precision=lbmhd.LBMHD_FP16_REL)
+    e = component_errors(mom, omom)
+    assert e["rho"] < 2e-5, e
+    for name, tol in zip(("rho_minus_1", "ux", "uy", "bx", "by"), FP16_REL_BOUNDS[steps]):
+        assert e[name] < tol, (name, e)
+    p = lbmhd.make_params(n, n, s, sm, 2.0, lbmhd.LBMHD_FP16)
+    with lbmhd.Lbmhd(p, *fields) as sim:
+        sim.step(steps)
+        e16 = component_errors(sim.moments(), omom)
+    assert e["rho_minus_1"] < 0.25 * e16["rho_minus_1"], (e, e16)
+
+
+@pytest.mark.parametrize("nx,ny,stencil", [(300, 70, 0), (33, 17, 1), (3, 3, 0), (129, 20, 0), (257, 9, 1)])
+def test_fp16_rel_short_runs_elementwise(nx, ny, stencil):
+    """Relative binary16 storage, population by population against the oracle after 6 steps
+    (strips of 128 columns with ragged tails, one-row bands, both stencils, unequal MRT rates):
+    measured at most 1.3e-5 for f and 1.9e-5 for g (g is stored as in binary16)."""
+    fields = smooth_random_fields(nx, ny, seed=3, amp_u=0.05, amp_b=0.04, amp_rho=0.02)
+    s, sm = mrt_rates(0.01), oracle.rate_from_diffusivity(0.015)
+    pops, ref, _, _ = run_pair(fields, s, sm, 2.0, 6, precision=lbmhd.LBMHD_FP16_REL, stencil=stencil)
+    assert np.max(np.abs(pops - ref)) < 6e-5
+
+
 @pytest.mark.parametrize("nx,ny,stencil", [(300, 70, 0), (33, 17, 1), (3, 3, 0), (129, 20, 0), (257, 9, 1)])
 def test_fp16_short_runs_elementwise(nx, ny, stencil):
     fields = smooth_random_fields(nx, ny, seed=3, amp_u=0.05, amp_b=0.04, amp_rho=0.02)
@@ -244,15 +287,22 @@ def test_full_size_2048_fp16_les_sampled():
 
 
 @pytest.mark.slow
+def test_full_size_2048_fp16_rel_les_sampled():
+    # relative binary16: one rounding of each stored value relative to the local velocity (f) or
+    # as binary16 (g)
+    _sampled_full_size(2048, lbmhd.LBMHD_FP16_REL, 2.0, 5e-4, 50, 1e-4)
+
+
+@pytest.mark.slow
 def test_full_size_2048_fp64_les_sampled():
     _sampled_full_size(2048, lbmhd.LBMHD_FP64, 2.0, 5e-4, 20, 1e-15)
 
 
 # The 4096^2 precision configuration (KH jet with d = N/64, nu = eta = 2e-4, Delta = 2) in all
-# three storage forms; tolerances as for 2048^2.
+# four storage forms; tolerances as for 2048^2.
 @pytest.mark.slow
 @pytest.mark.parametrize("precision,warm,tol", [(lbmhd.LBMHD_FP64, 10, 1e-15), (lbmhd.LBMHD_FP32, 30, 1e-7),
-                                                (lbmhd.LBMHD_FP16, 30, 1e-4)])
+                                                (lbmhd.LBMHD_FP16, 30, 1e-4), (lbmhd.LBMHD_FP16_REL, 30, 1e-4)])
 def test_full_size_4096_precision_config_sampled(precision, warm, tol):
     _sampled_full_size(4096, precision, 2.0, 2e-4, warm, tol, seed=3, delta_frac=1 / 64)
 
