@@ -49,12 +49,14 @@ MIN_TIMED_S = 1.0        # and at least this much timed time in all
 NU = ETA = 2e-3   # see the module docstring
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the fused FP32 kernel on the
-# 2048^2 workload, from an ncu capture; keyed by the SHA-256 of the kernel source it was taken
-# on (comments and whitespace removed), so a changed kernel reports null until it is measured
-# again.
+# 2048^2 workload, from an ncu capture of consecutive steps without ncu's L2 flush
+# (--cache-control none, the steady state of the timed loop); keyed by the SHA-256 of the kernel
+# source it was taken on (comments and whitespace removed), so a changed kernel reports null
+# until it is measured again.
 MEASURED_TRAFFIC = {
-    # profiles/fused_step_fp32_2048.md: (470.93 + 407.26 + 470.65 + 405.80) MB / 2 launches
-    ("9d0b3a599b3597ce", 2048, "fp32", 0.0): 877.32e6,
+    # profiles/fused_step_fp32_2048.md: mean of three launches after 40 steps,
+    # (425.22 + 454.69, 426.31 + 450.38, 425.26 + 451.91) MB
+    ("07b28e2cbae63153", 2048, "fp32", 0.0): 877.92e6,
 }
 
 
@@ -209,12 +211,16 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def precision_code(precision):
+    from paper_1705_09807_gb300 import lbmhd
+    return {"fp16": lbmhd.LBMHD_FP16, "fp16rel": lbmhd.LBMHD_FP16_REL, "fp32": lbmhd.LBMHD_FP32,
+            "fp64": lbmhd.LBMHD_FP64}[precision]
+
+
 def make_sim(n, precision, delta, stream=None, nu=NU, delta_frac=1 / 32, stencil=0):
     from paper_1705_09807_gb300 import lbmhd
     from paper_1705_09807_gb300.inputs import kh_jet
-    prec = {"fp16": lbmhd.LBMHD_FP16, "fp16rel": lbmhd.LBMHD_FP16_REL, "fp32": lbmhd.LBMHD_FP32,
-            "fp64": lbmhd.LBMHD_FP64}[precision]
-    p = lbmhd.lbmhd_params_srt(n, n, nu, nu, delta, prec)
+    p = lbmhd.lbmhd_params_srt(n, n, nu, nu, delta, precision_code(precision))
     p.cuda_stream = stream
     p.grad_stencil = stencil
     fields = kh_jet(n, u0=0.05, delta_frac=delta_frac, b0=0.02, seed=1)
@@ -265,7 +271,7 @@ def e2e_run(n, precision, delta, k):
     import torch
     from paper_1705_09807_gb300 import lbmhd
     from paper_1705_09807_gb300.inputs import kh_jet
-    prec = {"fp16": lbmhd.LBMHD_FP16, "fp32": lbmhd.LBMHD_FP32, "fp64": lbmhd.LBMHD_FP64}[precision]
+    prec = precision_code(precision)
     fields = kh_jet(n, u0=0.05, delta_frac=1 / 32, b0=0.02, seed=1)
     pin_in = [torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy() for _ in range(5)]
     for d, s in zip(pin_in, fields):
@@ -373,9 +379,12 @@ def run_ours(a, rank, ws, local):
                    "note": "median of the K-step windows, each bracketed by barrier + synchronize"},
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+        "dtype_note": "arithmetic type of the collision; storage in config.storage",
         "config": {"workload": workload_name(n, prec, delta), "grid": [n, n], "delta": delta,
                    "nu": NU, "eta": ETA, "initial_condition": "KH jet U0=0.05 d=N/32 B0=0.02 seed 1",
-                   "storage": "f_i - w_i and g_i in binary32" if prec == "fp32" else "binary64",
+                   "storage": {"fp32": "f_i - w_i and g_i in binary32", "fp64": "binary64",
+                               "fp16": "f_i - w_i and g_i in binary16",
+                               "fp16rel": "f_i - w_i (1 + 3 c_i.U) and g_i in binary16, U in 2 planes"}[prec],
                    "l2_policy": "working set %.0f MB > 129 MB L2, no flush" % (alg_bytes / 1e6),
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
