@@ -253,6 +253,15 @@ void lbmhd_closure_free(lbmhd_closure_t* c);
  * must outlive the attachment and must not be trained while attached. */
 int lbmhd_set_closure(lbmhd_t* h, lbmhd_closure_t* c);
 
+/* The correction planes that the attached closure gives the CURRENT state (what the next step
+ * would add: the fused network kernel of lbmhd_set_closure, run on its own), into the caller's
+ * device array corr [4][ny][nx] binary32 (xy stress, normal-stress difference, trace, electric
+ * field; physical units).  For inspecting or testing the learned correction; the state does not
+ * change.  Enqueued on the handle's stream (ordered with the legacy default stream when the
+ * handle owns its stream); LBMHD_ERR_INVALID without an attached closure or with corr NULL.  A
+ * wait that runs out in the network kernel is reported by the next synchronising call. */
+int lbmhd_closure_correction_device(lbmhd_t* h, float* corr);
+
 /* Failure-detection test hook.  With enable = 1, the first block of every following step
  * leaves out one of its staged-row copies, so its time-bounded wait (2 s) runs out: the block
  * records a timeout, drains its other copies and stops, no GPU fault occurs, and the next

@@ -576,6 +576,17 @@ int lbmhd_set_closure(lbmhd_t* h, lbmhd_closure_t* c) {
   return LBMHD_OK;
 }
 
+int lbmhd_closure_correction_device(lbmhd_t* h, float* corr) {
+  if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
+  if (!h->closure) return fail(h, LBMHD_ERR_INVALID, "no learned closure is attached");
+  if (!corr) return fail(h, LBMHD_ERR_INVALID, "corr is NULL");
+  int rc = order_in(h);
+  if (rc) return rc;
+  LB_CUDA(h, closure_correction(h->closure, h->precision, h->pops[h->cur], h->geom, corr, h->err_flag, h->stream));
+  h->launches += 1;
+  return order_out(h);
+}
+
 size_t lbmhd_state_bytes(const lbmhd_t* h) { return h ? h->state_bytes : 0; }
 
 int lbmhd_get_state(lbmhd_t* h, void* host_buf, size_t bytes) {

@@ -116,6 +116,7 @@ def load_library(path: str | None = None):
             "lbmhd_set_correction_device": (ctypes.c_int, [_H, ctypes.c_void_p]),
             "lbmhd_test_skip_row_copy": (ctypes.c_int, [_H, ctypes.c_int]),
             "lbmhd_set_closure": (ctypes.c_int, [_H, ctypes.c_void_p]),
+            "lbmhd_closure_correction_device": (ctypes.c_int, [_H, ctypes.c_void_p]),
             "lbmhd_closure_num_params": (ctypes.c_int, []),
             "lbmhd_closure_create": (ctypes.c_int, [ctypes.POINTER(_H), _F, _F, _F]),
             "lbmhd_closure_get_params": (ctypes.c_int, [_H, _F]),
@@ -595,6 +596,12 @@ class Closure:
             self.free()
         except Exception:
             pass
+
+
+def lbmhd_closure_correction_device(h, corr) -> None:
+    """The attached closure's correction planes of the current state into corr, a torch CUDA
+    float32 tensor [4, ny, nx] (contiguous)."""
+    _check(load_library().lbmhd_closure_correction_device(h, _dptr32(corr, corr.numel())), h)
 
 
 def lbmhd_detach_closure(h) -> None:

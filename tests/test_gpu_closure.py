@@ -243,3 +243,58 @@ def test_trained_network_beats_the_analytic_closure_a_priori():
         assert 1e-3 < a < 5e-3, rec  # the coarse run tracks the filtered DNS to ~0.2%
         assert 0.99 < net / a < 0.9995, rec
         assert abs(a / none - 1.0) < 1e-5, rec
+
+
+def _identity_paths(feats):
+    """Network parameters whose output channel o is tanh(tanh(x[feats[o]])) at every cell: the
+    centre tap of layer 1 routes feature feats[o] to hidden channel o, layers 2 and 3 pass hidden
+    channel o on (centre taps of weight 1), every other weight and every bias is zero."""
+    (W1, b1), (W2, b2), (W3, b3) = oc.unpack(np.zeros(oc.num_params()))
+    W1, W2, W3 = W1.copy(), W2.copy(), W3.copy()
+    for o, k in enumerate(feats):
+        W1[o, k, 1, 1] = 1.0
+        W2[o, o, 1, 1] = 1.0
+        W3[o, o, 1, 1] = 1.0
+    return np.concatenate([W1.ravel(), np.zeros(32), W2.ravel(), np.zeros(32), W3.ravel(), np.zeros(4)])
+
+
+@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32])
+def test_fused_network_features_match_the_oracle_per_channel(precision):
+    """The attached closure's kernel forms its 12 input features itself, in binary32, from the
+    pulled populations (u = J / rho, B and their central differences, over in_scale).  With a
+    network that passes feature k to an output unchanged but for tanh(tanh(.)) and bf16
+    rounding, its correction planes show those features cell by cell: they must equal the
+    oracle's features of the same state (binary64 moments of the GPU's own populations) to bf16
+    accuracy -- three passes of four channels cover all twelve."""
+    import torch
+    n = 64
+    fields = kh_jet(n, u0=0.05, delta_frac=1 / 16, b0=0.02, pert=2e-2, seed=8)
+    s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
+    p = lbmhd.make_params(n, n, s, sm, 2.0, precision)
+    with lbmhd.Lbmhd(p, *fields) as sim:
+        sim.step(60)
+        pops = sim.populations()
+        f, g = pops[:9], pops[9:].reshape(2, 9, n, n)
+        rho, ux, uy, bx, by = oracle.moments(f, g)
+        raw = oc.features(rho, ux, uy, bx, by, np.ones(12))
+        # scale every channel to a largest magnitude of 0.5 (the nonlinearity matters)
+        top = np.abs(raw).max(axis=(1, 2))
+        assert np.all(top > 0), top  # every channel carries a signal in this state
+        in_scale = (top / 0.5).astype(np.float32)
+        feats = raw / in_scale.astype(np.float64)[:, None, None]
+        out_scale = np.array([1.0, 2.0, 3.0, 4.0], dtype=np.float32)
+        corr = torch.empty((4, n, n), dtype=torch.float32, device="cuda")
+        for group in ((0, 1, 2, 3), (4, 5, 6, 7), (8, 9, 10, 11)):
+            theta = _identity_paths(group)
+            with lbmhd.Closure(theta, in_scale, out_scale) as cl:
+                cl.attach(sim.h)
+                lbmhd.lbmhd_closure_correction_device(sim.h, corr)
+                got = corr.cpu().numpy().astype(np.float64)
+                lbmhd.lbmhd_detach_closure(sim.h)
+            for o, k in enumerate(group):
+                want = out_scale[o] * np.tanh(np.tanh(feats[k]))
+                err = np.abs(got[o] - want)
+                # bf16 rounding of the feature and of two hidden activations (2^-9 relative
+                # each), the tanh.approx instruction: below 1.5% of the channel's range
+                assert err.max() < 1.5e-2 * np.abs(want).max(), (k, err.max(), np.abs(want).max())
+                assert np.sqrt(np.mean(err ** 2)) < 5e-3 * np.abs(want).max(), k
