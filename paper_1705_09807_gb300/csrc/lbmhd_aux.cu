@@ -1,5 +1,7 @@
 // Auxiliary kernels: equilibrium initialisation, macroscopic moments, canonical population
 // export and double-precision diagnostics.  None of them is on the per-step path.
+#include <type_traits>
+
 #include "lbmhd_internal.cuh"
 
 namespace lbmhd_gpu {
@@ -16,19 +18,23 @@ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >
 // Eq. feq, written as the deviation f_i^eq - w_i; Eq. geq.  Ghost columns written too.
 // REL (relative binary16 storage, LBMHD_FP16_REL): the cell's velocity reference U is its own
 // initial u rounded to binary16 (planes kQ, kQ + 1), and each stored f value is taken relative
-// to w_i (1 + 3 c_i . U).
+// to w_i (1 + 3 c_i . U).  The equilibria are evaluated in the storage's arithmetic type: binary64
+// for binary64 storage, binary32 otherwise (the stored value is rounded to binary32 or binary16
+// anyway, and GB300's binary64 rate is about 1/60 of its binary32 rate: the binary64 evaluation
+// took 2 ms for a 2048^2 binary32 state).
 template <typename T, bool REL = false>
 __global__ void init_eq_kernel(T* __restrict__ pops, StepGeom g, const double* __restrict__ rho,
                                const double* __restrict__ ux, const double* __restrict__ uy,
                                const double* __restrict__ bx, const double* __restrict__ by) {
+  using A = typename std::conditional<sizeof(T) == 8, double, float>::type;
   const long n = (long)g.nx * g.ny;
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
     const int x = (int)(c % g.nx), y = (int)(c / g.nx);
-    double Ux = 0.0, Uy = 0.0;
+    A Ux = A(0), Uy = A(0);
     if constexpr (REL) {
       const __half hx = __double2half(ux[c]), hy = __double2half(uy[c]);
-      Ux = (double)__half2float(hx);
-      Uy = (double)__half2float(hy);
+      Ux = (A)__half2float(hx);
+      Uy = (A)__half2float(hy);
       const size_t o = (size_t)y * g.pitch + kXOff + x;
       const T u2[2] = {hx, hy};
 #pragma unroll
@@ -42,16 +48,16 @@ __global__ void init_eq_kernel(T* __restrict__ pops, StepGeom g, const double* _
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const long s = (long)wrapi(y + vy(i), g.ny) * g.nx + wrapi(x + vx(i), g.nx);
-      const double r = rho[s], u = ux[s], v = uy[s], b = bx[s], d = by[s];
-      const double cu = vx(i) * u + vy(i) * v;
-      const double cb = vx(i) * b + vy(i) * d;
-      const double csq = (double)(vx(i) * vx(i) + vy(i) * vy(i));
-      const double w = wt(i);
-      double fdev = w * (r - 1.0) + w * r * (3.0 * cu + 4.5 * cu * cu - 1.5 * (u * u + v * v)) +
-                    4.5 * w * (0.5 * (b * b + d * d) * csq - cb * cb);
-      if (REL) fdev -= 3.0 * w * (vx(i) * Ux + vy(i) * Uy);
-      const double gx = w * (b + 3.0 * (cu * b - cb * u));
-      const double gy = w * (d + 3.0 * (cu * d - cb * v));
+      const A r = (A)rho[s], u = (A)ux[s], v = (A)uy[s], b = (A)bx[s], d = (A)by[s];
+      const A cu = vx(i) * u + vy(i) * v;
+      const A cb = vx(i) * b + vy(i) * d;
+      const A csq = (A)(vx(i) * vx(i) + vy(i) * vy(i));
+      const A w = (A)wt(i);
+      A fdev = w * (r - A(1)) + w * r * (A(3) * cu + A(4.5) * cu * cu - A(1.5) * (u * u + v * v)) +
+               A(4.5) * w * (A(0.5) * (b * b + d * d) * csq - cb * cb);
+      if (REL) fdev -= A(3) * w * (vx(i) * Ux + vy(i) * Uy);
+      const A gx = w * (b + A(3) * (cu * b - cb * u));
+      const A gy = w * (d + A(3) * (cu * d - cb * v));
       const size_t o = (size_t)y * g.pitch + kXOff + x;
       const T vals[3] = {store_as<T>(fdev), store_as<T>(gx), store_as<T>(gy)};
 #pragma unroll
