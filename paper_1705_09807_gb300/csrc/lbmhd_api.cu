@@ -233,8 +233,18 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
       return rc_map;
     }
   }
-  // zero the row padding once so checkpoints are deterministic
-  for (int i = 0; i < 2; ++i) LB_INIT(cudaMemsetAsync(h->pops[i], 0, h->state_bytes, h->stream));
+  // zero the row padding once so checkpoints are deterministic: physical columns [0, kXOff - 2)
+  // and [nx + kXOff + 2, plane) of every plane row (the interior and the ghost columns are
+  // written by the initialisation in copy 0 and by the first step in copy 1)
+  {
+    const size_t e = h->elem, row = g.plane * e, rows = (size_t)h->nplanes * g.ny;
+    const size_t right0 = (size_t)g.nx + kXOff + 2, right = (size_t)g.plane - right0;
+    for (int i = 0; i < 2; ++i) {
+      char* base = static_cast<char*>(h->pops[i]);
+      LB_INIT(cudaMemset2DAsync(base, row, 0, (kXOff - 2) * e, rows, h->stream));
+      if (right) LB_INIT(cudaMemset2DAsync(base + right0 * e, row, 0, right * e, rows, h->stream));
+    }
+  }
 #undef LB_INIT
   *out = h;
   return LBMHD_OK;

@@ -110,8 +110,14 @@ __global__ void moments_kernel(const T* __restrict__ pops, StepGeom g, double* _
     }
     const double rr = 1.0 + r;
     rho[c] = rr;
-    ux[c] = jx / rr;
-    uy[c] = jy / rr;
+    if (sizeof(T) == 8) {
+      ux[c] = jx / rr;
+      uy[c] = jy / rr;
+    } else {  // binary32 / binary16 storage: a binary32 division (GB300's binary64 divide is slow)
+      const float ir = 1.f / (float)rr;
+      ux[c] = (double)((float)jx * ir);
+      uy[c] = (double)((float)jy * ir);
+    }
     bx[c] = sbx;
     by[c] = sby;
   }
