@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <cstdint>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -156,6 +157,38 @@ int make_tensor_map(lbmhd_t* h, void* base, CUtensorMap* map, int box_planes = 9
   return LBMHD_OK;
 }
 
+// Device address of a host array of `bytes` bytes that kernels may write directly: the array
+// lies entirely inside one page-locked allocation (cudaHostAlloc, cudaMallocHost,
+// cudaHostRegister) that the current device maps.  nullptr otherwise -- pageable memory, or an
+// extent that cannot be had -- and the caller stages through device memory instead.
+void* mapped_host_array(void* ptr, size_t bytes) {
+  using PointerGetAttributeFn = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+  static const PointerGetAttributeFn get = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 4000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return static_cast<PointerGetAttributeFn>(nullptr);
+    return reinterpret_cast<PointerGetAttributeFn>(f);
+  }();
+  if (!get || !ptr) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  const CUdeviceptr d = (CUdeviceptr)(uintptr_t)a.devicePointer;
+  CUdeviceptr start = 0;
+  size_t size = 0;
+  if (get(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, d) != CUDA_SUCCESS ||
+      get(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, d) != CUDA_SUCCESS)
+    return nullptr;
+  if (d < start || d - start > size || size - (d - start) < bytes) return nullptr;
+  return a.devicePointer;
+}
+
 // Status of the step kernels' pipeline waits (call after synchronising the stream).
 int check_step_status(lbmhd_t* h) {
   unsigned v = 0;
@@ -168,7 +201,11 @@ int check_step_status(lbmhd_t* h) {
   return LBMHD_OK;
 }
 
-int create(lbmhd_t** out, const lbmhd_params* p) {
+// Handle with its device memory and tensor maps (no initial state).  With host_fields (the five
+// initial fields of lbmhd_init), their host-to-device copies into the moment-field buffer start as
+// soon as that buffer exists: they run over the host link while the population copies are
+// allocated.
+int create(lbmhd_t** out, const lbmhd_params* p, const double* const* host_fields = nullptr) {
   if (!out) return fail(nullptr, LBMHD_ERR_INVALID, "out is NULL");
   *out = nullptr;
   int rc = check_params(p);
@@ -218,8 +255,12 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
   }
   LB_INIT(cudaEventCreateWithFlags(&h->ev_a, cudaEventDisableTiming));
   LB_INIT(cudaEventCreateWithFlags(&h->ev_b, cudaEventDisableTiming));
-  for (int i = 0; i < 2; ++i) LB_INIT(cudaMalloc(&h->pops[i], h->state_bytes));
   LB_INIT(cudaMalloc(&h->fields, 5 * ncell * sizeof(double)));
+  if (host_fields)
+    for (int k = 0; k < 5; ++k)
+      LB_INIT(cudaMemcpyAsync(h->fields + k * ncell, host_fields[k], ncell * sizeof(double),
+                              cudaMemcpyHostToDevice, h->stream));
+  for (int i = 0; i < 2; ++i) LB_INIT(cudaMalloc(&h->pops[i], h->state_bytes));
   LB_INIT(cudaMalloc(&h->partials, (size_t)kDiagBlocks * kDiagSlots * sizeof(double)));
   LB_INIT(cudaMalloc(&h->diag_out, kDiagSlots * sizeof(double)));
   LB_INIT(cudaMalloc(&h->err_flag, sizeof(unsigned)));
@@ -381,19 +422,10 @@ int lbmhd_init(lbmhd_t** out, const lbmhd_params* p, const double* rho, const do
   if (!check_fields(rho, ux, uy, bx, by))
     return fail(nullptr, LBMHD_ERR_INVALID, "a field pointer is NULL");
   lbmhd_t* h = nullptr;
-  int rc = create(&h, p);
+  const double* src[5] = {rho, ux, uy, bx, by};
+  int rc = create(&h, p, src);  // copies the fields into h->fields on h->stream
   if (rc) return rc;
   const size_t ncell = (size_t)p->nx * p->ny;
-  const double* src[5] = {rho, ux, uy, bx, by};
-  for (int k = 0; k < 5; ++k) {
-    cudaError_t e = cudaMemcpyAsync(h->fields + k * ncell, src[k], ncell * sizeof(double),
-                                    cudaMemcpyHostToDevice, h->stream);
-    if (e != cudaSuccess) {
-      rc = cuda_fail(nullptr, e, "copying the initial fields to the device");
-      free_all(h);
-      return rc;
-    }
-  }
   cudaError_t e = launch_init_eq(h->precision, h->pops[0], h->geom, h->fields, h->fields + ncell,
                                  h->fields + 2 * ncell, h->fields + 3 * ncell,
                                  h->fields + 4 * ncell, h->stream);
@@ -473,14 +505,26 @@ int lbmhd_moments(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx, d
   if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
   if (!check_fields(rho, ux, uy, bx, by)) return fail(h, LBMHD_ERR_INVALID, "a field pointer is NULL");
   const size_t ncell = (size_t)h->p.nx * h->p.ny;
-  double* f = h->fields;
-  LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, f, f + ncell, f + 2 * ncell,
-                            f + 3 * ncell, f + 4 * ncell, h->stream));
-  h->launches += 1;
   double* dst[5] = {rho, ux, uy, bx, by};
-  for (int k = 0; k < 5; ++k)
-    LB_CUDA(h, cudaMemcpyAsync(dst[k], f + k * ncell, ncell * sizeof(double), cudaMemcpyDeviceToHost,
-                               h->stream));
+  double* direct[5];
+  bool mapped = true;
+  for (int k = 0; k < 5; ++k) {
+    direct[k] = static_cast<double*>(mapped_host_array(dst[k], ncell * sizeof(double)));
+    mapped = mapped && direct[k];
+  }
+  if (mapped) {  // page-locked outputs: the read-out kernel writes them over the host link
+    LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, direct[0], direct[1],
+                              direct[2], direct[3], direct[4], h->stream));
+    h->launches += 1;
+  } else {  // pageable outputs: through the device field buffer
+    double* f = h->fields;
+    LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, f, f + ncell, f + 2 * ncell,
+                              f + 3 * ncell, f + 4 * ncell, h->stream));
+    h->launches += 1;
+    for (int k = 0; k < 5; ++k)
+      LB_CUDA(h, cudaMemcpyAsync(dst[k], f + k * ncell, ncell * sizeof(double),
+                                 cudaMemcpyDeviceToHost, h->stream));
+  }
   LB_CUDA(h, cudaStreamSynchronize(h->stream));
   return check_step_status(h);
 }

@@ -90,6 +90,21 @@ __device__ __forceinline__ void pull_cell(const T* __restrict__ pops, const Step
   }
 }
 
+// Sum of binary32 values kept exactly as the unevaluated pair hi + lo (Knuth's TwoSum: the
+// rounding error of each binary32 addition is itself a binary32 value).  Nine stored binary32 or
+// binary16 values sum to the binary64 result up to one rounding of lo, with binary32 arithmetic
+// only: GB300's binary64 rate (about 1/60 of binary32) made the binary64 sums of the moments
+// read-out take 0.55 ms at 2048^2, four times the kernel's memory time.
+struct PairSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float s = hi + v, bv = s - hi;
+    lo += (hi - (s - bv)) + (v - bv);
+    hi = s;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 template <typename T, bool REL = false>
 __global__ void moments_kernel(const T* __restrict__ pops, StepGeom g, double* __restrict__ rho,
                                double* __restrict__ ux, double* __restrict__ uy,
@@ -97,18 +112,44 @@ __global__ void moments_kernel(const T* __restrict__ pops, StepGeom g, double* _
   const long n = (long)g.nx * g.ny;
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
     const int x = (int)(c % g.nx), y = (int)(c / g.nx);
-    double v[27];
-    pull_cell<T, REL>(pops, g, x, y, v);
-    double r = 0, jx = 0, jy = 0, sbx = 0, sby = 0;
+    double rr, jx, jy, sbx, sby;
+    if constexpr (sizeof(T) == 8 || REL) {  // binary64 sums (REL: the decoded values are binary64)
+      double v[27];
+      pull_cell<T, REL>(pops, g, x, y, v);
+      double r = 0;
+      jx = jy = sbx = sby = 0;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      r += v[i];
-      jx += vx(i) * v[i];
-      jy += vy(i) * v[i];
-      sbx += v[9 + i];
-      sby += v[18 + i];
+      for (int i = 0; i < 9; ++i) {
+        r += v[i];
+        jx += vx(i) * v[i];
+        jy += vy(i) * v[i];
+        sbx += v[9 + i];
+        sby += v[18 + i];
+      }
+      rr = 1.0 + r;
+    } else {  // binary32 / binary16 storage: exact binary32 pair sums of the pulled values
+      PairSum r, px, py, qx, qy;
+#pragma unroll
+      for (int q = 0; q < 27; ++q) {
+        const int i = q % 9;
+        const int sx = wrapi(x - vx(i), g.nx), sy = wrapi(y - vy(i), g.ny);
+        const float v = load_as<float>(pops[(size_t)plane_of(q) * g.plane + (size_t)sy * g.pitch + kXOff + sx]);
+        if (q < 9) {
+          r.add(v);
+          if (vx(i)) px.add(vx(i) > 0 ? v : -v);
+          if (vy(i)) py.add(vy(i) > 0 ? v : -v);
+        } else if (q < 18) {
+          qx.add(v);
+        } else {
+          qy.add(v);
+        }
+      }
+      rr = 1.0 + r.value();
+      jx = px.value();
+      jy = py.value();
+      sbx = qx.value();
+      sby = qy.value();
     }
-    const double rr = 1.0 + r;
     rho[c] = rr;
     if (sizeof(T) == 8) {
       ux[c] = jx / rr;

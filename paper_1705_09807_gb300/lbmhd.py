@@ -224,8 +224,16 @@ def lbmhd_step(h, nsteps: int) -> None:
     _check(load_library().lbmhd_step(h, int(nsteps)), h)
 
 
-def lbmhd_moments(h, ny: int, nx: int):
-    outs = [np.empty((ny, nx)) for _ in range(5)]
+def lbmhd_moments(h, ny: int, nx: int, out=None):
+    """(rho, ux, uy, bx, by) as host arrays: new pageable arrays, or the five C-contiguous
+    float64 [ny, nx] arrays of `out` (page-locked ones are written by the kernel directly)."""
+    if out is None:
+        outs = [np.empty((ny, nx)) for _ in range(5)]
+    else:
+        outs = list(out)
+        if len(outs) != 5 or not all(isinstance(o, np.ndarray) and o.dtype == np.float64 and
+                                     o.shape == (ny, nx) and o.flags.c_contiguous for o in outs):
+            raise ValueError(f"out must be five C-contiguous float64 arrays of shape {(ny, nx)}")
     _check(load_library().lbmhd_moments(h, *(o.ctypes.data_as(_D) for o in outs)), h)
     return tuple(outs)
 
@@ -352,8 +360,8 @@ class Lbmhd:
         lbmhd_step(self.h, n)
         return self
 
-    def moments(self):
-        return lbmhd_moments(self.h, self.ny, self.nx)
+    def moments(self, out=None):
+        return lbmhd_moments(self.h, self.ny, self.nx, out)
 
     def moments_device(self, outs):
         lbmhd_moments_device(self.h, outs)

@@ -47,6 +47,53 @@ def test_checkpoint_resume_bitwise(precision):
         assert np.array_equal(other.populations(), a)
 
 
+@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32, lbmhd.LBMHD_FP16,
+                                       lbmhd.LBMHD_FP16_REL])
+def test_page_locked_host_arrays_give_the_same_bits(precision):
+    """Page-locked initial fields (copied while the handle allocates) and page-locked outputs
+    (written by the read-out kernel directly) give the same state and moments as pageable ones,
+    also for output arrays at offsets inside one page-locked block."""
+    import torch
+    nx, ny = 96, 80
+    fields = smooth_random_fields(nx, ny, seed=12, amp_u=0.04, amp_b=0.03, amp_rho=0.01)
+    pin_in = torch.empty((5, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    pin_in[...] = np.stack(fields)
+    block = torch.empty((6, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
+    p = lbmhd.make_params(nx, ny, s, sm, 2.0, precision)
+    with lbmhd.Lbmhd(p, *fields) as a, lbmhd.Lbmhd(p, *pin_in) as b:
+        a.step(23)
+        b.step(23)
+        assert np.array_equal(a.populations(), b.populations())
+        want = a.moments()
+        launches = b.launches
+        got = b.moments(out=[block[k + 1] for k in range(5)])
+        assert b.launches == launches + 1
+        assert all(g.ctypes.data == block[k + 1].ctypes.data for k, g in enumerate(got))
+    for x, y in zip(got, want):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP32, lbmhd.LBMHD_FP16])
+def test_binary32_read_out_matches_binary64_moments_of_the_state(precision):
+    """The binary32 and binary16 forms read the moments out with binary32 pair sums (each
+    addition's rounding error kept): rho, bx and by equal the binary64 moments of the same stored
+    populations to binary64 rounding; u takes one binary32 division (four binary32 roundings)."""
+    nx, ny = 96, 80
+    fields = smooth_random_fields(nx, ny, seed=13, amp_u=0.05, amp_b=0.03, amp_rho=0.02)
+    s, sm = oracle.srt_rates(0.002), oracle.rate_from_diffusivity(0.002)
+    with lbmhd.Lbmhd(lbmhd.make_params(nx, ny, s, sm, 2.0, precision), *fields) as sim:
+        sim.step(31)
+        pops = sim.populations()
+        got = sim.moments()
+    ref = oracle.moments(pops[:9], pops[9:].reshape(2, 9, ny, nx))
+    for k in (0, 3, 4):
+        assert np.max(np.abs(got[k] - ref[k])) < 4e-15
+    for k in (1, 2):
+        assert np.all(np.abs(got[k] - ref[k]) <= 2.5e-7 * np.abs(ref[k]) + 1e-15)
+    assert np.max(np.abs(ref[1])) > 0.01
+
+
 def test_runs_are_deterministic_and_graph_free_path_agrees():
     import torch
     fields = kh_jet(160, seed=5)
