@@ -161,7 +161,7 @@ int make_tensor_map(lbmhd_t* h, void* base, CUtensorMap* map, int box_planes = 9
 // lies entirely inside one page-locked allocation (cudaHostAlloc, cudaMallocHost,
 // cudaHostRegister) that the current device maps.  nullptr otherwise -- pageable memory, or an
 // extent that cannot be had -- and the caller stages through device memory instead.
-void* mapped_host_array(void* ptr, size_t bytes) {
+void* mapped_host_array(const void* ptr, size_t bytes) {
   using PointerGetAttributeFn = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
   static const PointerGetAttributeFn get = [] {
     void* f = nullptr;
@@ -189,6 +189,19 @@ void* mapped_host_array(void* ptr, size_t bytes) {
   return a.devicePointer;
 }
 
+// The device moment-field buffer (5 x nx*ny binary64), allocated on the first call that stages
+// through it: page-locked host arrays and the device entry points never need it.
+int ensure_fields(lbmhd_t* h) {
+  if (!h->fields) {
+    cudaError_t e = cudaMalloc(&h->fields, 5 * (size_t)h->p.nx * h->p.ny * sizeof(double));
+    if (e != cudaSuccess) {
+      h->fields = nullptr;
+      return cuda_fail(h, e, "allocating the moment-field buffer");
+    }
+  }
+  return LBMHD_OK;
+}
+
 // Status of the step kernels' pipeline waits (call after synchronising the stream).
 int check_step_status(lbmhd_t* h) {
   unsigned v = 0;
@@ -201,11 +214,8 @@ int check_step_status(lbmhd_t* h) {
   return LBMHD_OK;
 }
 
-// Handle with its device memory and tensor maps (no initial state).  With host_fields (the five
-// initial fields of lbmhd_init), their host-to-device copies into the moment-field buffer start as
-// soon as that buffer exists: they run over the host link while the population copies are
-// allocated.
-int create(lbmhd_t** out, const lbmhd_params* p, const double* const* host_fields = nullptr) {
+// Handle with its device memory and tensor maps (no initial state).
+int create(lbmhd_t** out, const lbmhd_params* p) {
   if (!out) return fail(nullptr, LBMHD_ERR_INVALID, "out is NULL");
   *out = nullptr;
   int rc = check_params(p);
@@ -255,11 +265,6 @@ int create(lbmhd_t** out, const lbmhd_params* p, const double* const* host_field
   }
   LB_INIT(cudaEventCreateWithFlags(&h->ev_a, cudaEventDisableTiming));
   LB_INIT(cudaEventCreateWithFlags(&h->ev_b, cudaEventDisableTiming));
-  LB_INIT(cudaMalloc(&h->fields, 5 * ncell * sizeof(double)));
-  if (host_fields)
-    for (int k = 0; k < 5; ++k)
-      LB_INIT(cudaMemcpyAsync(h->fields + k * ncell, host_fields[k], ncell * sizeof(double),
-                              cudaMemcpyHostToDevice, h->stream));
   for (int i = 0; i < 2; ++i) LB_INIT(cudaMalloc(&h->pops[i], h->state_bytes));
   LB_INIT(cudaMalloc(&h->partials, (size_t)kDiagBlocks * kDiagSlots * sizeof(double)));
   LB_INIT(cudaMalloc(&h->diag_out, kDiagSlots * sizeof(double)));
@@ -274,18 +279,9 @@ int create(lbmhd_t** out, const lbmhd_params* p, const double* const* host_field
       return rc_map;
     }
   }
-  // zero the row padding once so checkpoints are deterministic: physical columns [0, kXOff - 2)
-  // and [nx + kXOff + 2, plane) of every plane row (the interior and the ghost columns are
-  // written by the initialisation in copy 0 and by the first step in copy 1)
-  {
-    const size_t e = h->elem, row = g.plane * e, rows = (size_t)h->nplanes * g.ny;
-    const size_t right0 = (size_t)g.nx + kXOff + 2, right = (size_t)g.plane - right0;
-    for (int i = 0; i < 2; ++i) {
-      char* base = static_cast<char*>(h->pops[i]);
-      LB_INIT(cudaMemset2DAsync(base, row, 0, (kXOff - 2) * e, rows, h->stream));
-      if (right) LB_INIT(cudaMemset2DAsync(base + right0 * e, row, 0, right * e, rows, h->stream));
-    }
-  }
+  // zero the row padding once so checkpoints are deterministic (the interior and the ghost
+  // columns are written by the initialisation in copy 0 and by the first step in copy 1)
+  LB_INIT(launch_zero_pads(h->pops[0], h->pops[1], g, h->nplanes, h->elem, h->stream));
 #undef LB_INIT
   *out = h;
   return LBMHD_OK;
@@ -422,13 +418,38 @@ int lbmhd_init(lbmhd_t** out, const lbmhd_params* p, const double* rho, const do
   if (!check_fields(rho, ux, uy, bx, by))
     return fail(nullptr, LBMHD_ERR_INVALID, "a field pointer is NULL");
   lbmhd_t* h = nullptr;
-  const double* src[5] = {rho, ux, uy, bx, by};
-  int rc = create(&h, p, src);  // copies the fields into h->fields on h->stream
+  int rc = create(&h, p);
   if (rc) return rc;
   const size_t ncell = (size_t)p->nx * p->ny;
-  cudaError_t e = launch_init_eq(h->precision, h->pops[0], h->geom, h->fields, h->fields + ncell,
-                                 h->fields + 2 * ncell, h->fields + 3 * ncell,
-                                 h->fields + 4 * ncell, h->stream);
+  const double* src[5] = {rho, ux, uy, bx, by};
+  const double* in[5];
+  bool mapped = true;
+  for (int k = 0; k < 5; ++k) {
+    in[k] = static_cast<const double*>(mapped_host_array(src[k], ncell * sizeof(double)));
+    mapped = mapped && in[k];
+  }
+  if (!mapped) {  // pageable fields: through the device field buffer; page-locked ones are read
+                  // by the initialisation kernel directly over the host link
+    rc = ensure_fields(h);
+    if (rc) {
+      g_tls_error = h->err;
+      free_all(h);
+      return rc;
+    }
+  }
+  if (!mapped)
+    for (int k = 0; k < 5; ++k) {
+      in[k] = h->fields + k * ncell;
+      cudaError_t e = cudaMemcpyAsync(h->fields + k * ncell, src[k], ncell * sizeof(double),
+                                      cudaMemcpyHostToDevice, h->stream);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(nullptr, e, "copying the initial fields to the device");
+        free_all(h);
+        return rc;
+      }
+    }
+  cudaError_t e = launch_init_eq(h->precision, h->pops[0], h->geom, in[0], in[1], in[2], in[3],
+                                 in[4], h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     rc = cuda_fail(nullptr, e, "equilibrium initialisation");
@@ -517,6 +538,8 @@ int lbmhd_moments(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx, d
                               direct[2], direct[3], direct[4], h->stream));
     h->launches += 1;
   } else {  // pageable outputs: through the device field buffer
+    int rc = ensure_fields(h);
+    if (rc) return rc;
     double* f = h->fields;
     LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, f, f + ncell, f + 2 * ncell,
                               f + 3 * ncell, f + 4 * ncell, h->stream));
@@ -551,6 +574,8 @@ int lbmhd_diagnostics(lbmhd_t* h, double* out) {
   if (!h) return fail(nullptr, LBMHD_ERR_INVALID, "handle is NULL");
   if (!out) return fail(h, LBMHD_ERR_INVALID, "out is NULL");
   const size_t ncell = (size_t)h->p.nx * h->p.ny;
+  int frc = ensure_fields(h);
+  if (frc) return frc;
   double* f = h->fields;
   LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, f, f + ncell, f + 2 * ncell,
                             f + 3 * ncell, f + 4 * ncell, h->stream));
@@ -580,6 +605,8 @@ int lbmhd_energy_spectrum(lbmhd_t* h, int nbins, double* e_kin, double* e_mag) {
   double* dk = reinterpret_cast<double*>(static_cast<char*>(h->spec_work) + wb);
   double* dm = dk + n;
   const size_t ncell = (size_t)n * n;
+  int frc = ensure_fields(h);
+  if (frc) return frc;
   double* f = h->fields;
   LB_CUDA(h, launch_moments(h->precision, h->pops[h->cur], h->geom, f, f + ncell, f + 2 * ncell,
                             f + 3 * ncell, f + 4 * ncell, h->stream));

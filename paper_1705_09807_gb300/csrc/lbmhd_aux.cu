@@ -1,5 +1,6 @@
 // Auxiliary kernels: equilibrium initialisation, macroscopic moments, canonical population
 // export and double-precision diagnostics.  None of them is on the per-step path.
+#include <algorithm>
 #include <type_traits>
 
 #include "lbmhd_internal.cuh"
@@ -18,55 +19,104 @@ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >
 // Eq. feq, written as the deviation f_i^eq - w_i; Eq. geq.  Ghost columns written too.
 // REL (relative binary16 storage, LBMHD_FP16_REL): the cell's velocity reference U is its own
 // initial u rounded to binary16 (planes kQ, kQ + 1), and each stored f value is taken relative
-// to w_i (1 + 3 c_i . U).  The equilibria are evaluated in the storage's arithmetic type: binary64
-// for binary64 storage, binary32 otherwise (the stored value is rounded to binary32 or binary16
-// anyway, and GB300's binary64 rate is about 1/60 of its binary32 rate: the binary64 evaluation
-// took 2 ms for a 2048^2 binary32 state).
+// to w_i (1 + 3 c_i . U).  The equilibria are evaluated in the storage's arithmetic type A:
+// binary64 for binary64 storage, binary32 otherwise (the stored value is rounded to binary32 or
+// binary16 anyway, and GB300's binary64 rate is about 1/60 of its binary32 rate).
+//
+// One block per strip of kInitCols columns and band of kInitRows rows.  The fields of rows
+// y - 1, y, y + 1 sit in a ring of three shared-memory rows (columns x0 - 1 .. x0 + kInitCols,
+// periodic), each value read and converted to A once, with |u|^2 and |B|^2 formed once per cell:
+// the nine equilibria of a cell then read only shared memory.  Only the two halo rows of each
+// band are read twice, so the input arrays may be page-locked host memory read over the host
+// link.  (Converting every binary64 input nine times, once per direction, took 0.45 ms at 2048^2
+// on GB300's binary64 conversion rate.)
+constexpr int kInitCols = 128, kInitRows = 32;
+
 template <typename T, bool REL = false>
-__global__ void init_eq_kernel(T* __restrict__ pops, StepGeom g, const double* __restrict__ rho,
-                               const double* __restrict__ ux, const double* __restrict__ uy,
-                               const double* __restrict__ bx, const double* __restrict__ by) {
+__global__ void __launch_bounds__(kInitCols)
+    init_eq_kernel(T* __restrict__ pops, StepGeom g, const double* __restrict__ rho,
+                   const double* __restrict__ ux, const double* __restrict__ uy,
+                   const double* __restrict__ bx, const double* __restrict__ by) {
   using A = typename std::conditional<sizeof(T) == 8, double, float>::type;
-  const long n = (long)g.nx * g.ny;
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
-    const int x = (int)(c % g.nx), y = (int)(c / g.nx);
-    A Ux = A(0), Uy = A(0);
-    if constexpr (REL) {
-      const __half hx = __double2half(ux[c]), hy = __double2half(uy[c]);
-      Ux = (A)__half2float(hx);
-      Uy = (A)__half2float(hy);
-      const size_t o = (size_t)y * g.pitch + kXOff + x;
-      const T u2[2] = {hx, hy};
-#pragma unroll
-      for (int comp = 0; comp < 2; ++comp) {
-        T* pl = pops + (size_t)(kQ + comp) * g.plane + o;
-        pl[0] = u2[comp];
-        if (x < 2) pl[g.nx] = u2[comp];
-        if (x >= g.nx - 2) pl[-g.nx] = u2[comp];
+  constexpr int W = kInitCols + 2;
+  constexpr int NV = REL ? 9 : 7;  // rho, ux, uy, bx, by, |u|^2, |B|^2 (REL: U_x, U_y in binary16)
+  __shared__ A ring[3][NV][W];
+  const int x0 = blockIdx.x * kInitCols;
+  const int cols = min(kInitCols, g.nx - x0);
+  const int nbands = (g.ny + kInitRows - 1) / kInitRows;
+  for (int band = blockIdx.y; band < nbands; band += gridDim.y) {
+    const int y0 = band * kInitRows, y1 = min(y0 + kInitRows, g.ny);
+    // field row yy (in [-1, ny], periodic) into ring slot (yy + 3) mod 3
+    auto load_row = [&](int yy) {
+      const int slot = (yy + 3) % 3;
+      const size_t row = (size_t)wrapi(yy, g.ny) * g.nx;
+      for (int j = threadIdx.x; j < cols + 2; j += blockDim.x) {
+        const size_t c = row + wrapi(x0 - 1 + j, g.nx);
+        const double du = ux[c], dv = uy[c];
+        const A r = (A)rho[c], u = (A)du, v = (A)dv, bb = (A)bx[c], d = (A)by[c];
+        A* e = &ring[slot][0][j];
+        e[0 * W] = r;
+        e[1 * W] = u;
+        e[2 * W] = v;
+        e[3 * W] = bb;
+        e[4 * W] = d;
+        e[5 * W] = u * u + v * v;
+        e[6 * W] = bb * bb + d * d;
+        if constexpr (REL) {
+          e[7 * W] = (A)__half2float(__double2half(du));
+          e[8 * W] = (A)__half2float(__double2half(dv));
+        }
       }
-    }
+    };
+    // (the previous band ended with a block barrier: its readers of the ring are done)
+    load_row(y0 - 1);
+    load_row(y0);
+    for (int y = y0; y < y1; ++y) {
+      load_row(y + 1);
+      __syncthreads();
+      const int jx = threadIdx.x + 1;
+      const int x = x0 + threadIdx.x;
+      if (threadIdx.x < cols) {
+        const size_t o = (size_t)y * g.pitch + kXOff + x;
+        A Ux = A(0), Uy = A(0);
+        if constexpr (REL) {
+          const A* e = &ring[y % 3][0][jx];
+          Ux = e[7 * W];
+          Uy = e[8 * W];
+          const T u2[2] = {store_as<T>(Ux), store_as<T>(Uy)};  // exact: Ux, Uy are binary16 values
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const long s = (long)wrapi(y + vy(i), g.ny) * g.nx + wrapi(x + vx(i), g.nx);
-      const A r = (A)rho[s], u = (A)ux[s], v = (A)uy[s], b = (A)bx[s], d = (A)by[s];
-      const A cu = vx(i) * u + vy(i) * v;
-      const A cb = vx(i) * b + vy(i) * d;
-      const A csq = (A)(vx(i) * vx(i) + vy(i) * vy(i));
-      const A w = (A)wt(i);
-      A fdev = w * (r - A(1)) + w * r * (A(3) * cu + A(4.5) * cu * cu - A(1.5) * (u * u + v * v)) +
-               A(4.5) * w * (A(0.5) * (b * b + d * d) * csq - cb * cb);
-      if (REL) fdev -= A(3) * w * (vx(i) * Ux + vy(i) * Uy);
-      const A gx = w * (b + A(3) * (cu * b - cb * u));
-      const A gy = w * (d + A(3) * (cu * d - cb * v));
-      const size_t o = (size_t)y * g.pitch + kXOff + x;
-      const T vals[3] = {store_as<T>(fdev), store_as<T>(gx), store_as<T>(gy)};
+          for (int comp = 0; comp < 2; ++comp) {
+            T* pl = pops + (size_t)(kQ + comp) * g.plane + o;
+            pl[0] = u2[comp];
+            if (x < 2) pl[g.nx] = u2[comp];
+            if (x >= g.nx - 2) pl[-g.nx] = u2[comp];
+          }
+        }
 #pragma unroll
-      for (int comp = 0; comp < 3; ++comp) {
-        T* pl = pops + (size_t)plane_of(9 * comp + i) * g.plane + o;
-        pl[0] = vals[comp];
-        if (x < 2) pl[g.nx] = vals[comp];          // ghosts of columns 0, 1 at nx, nx + 1
-        if (x >= g.nx - 2) pl[-g.nx] = vals[comp];  // ghosts of columns nx-2, nx-1 at -2, -1
+        for (int i = 0; i < 9; ++i) {
+          const A* e = &ring[(y + vy(i) + 3) % 3][0][jx + vx(i)];
+          const A r = e[0 * W], u = e[1 * W], v = e[2 * W], b = e[3 * W], d = e[4 * W];
+          const A usq = e[5 * W], bsq = e[6 * W];
+          const A cu = vx(i) * u + vy(i) * v;
+          const A cb = vx(i) * b + vy(i) * d;
+          const A csq = (A)(vx(i) * vx(i) + vy(i) * vy(i));
+          const A w = (A)wt(i);
+          A fdev = w * (r - A(1)) + w * r * (A(3) * cu + A(4.5) * cu * cu - A(1.5) * usq) +
+                   A(4.5) * w * (A(0.5) * bsq * csq - cb * cb);
+          if (REL) fdev -= A(3) * w * (vx(i) * Ux + vy(i) * Uy);
+          const A gx = w * (b + A(3) * (cu * b - cb * u));
+          const A gy = w * (d + A(3) * (cu * d - cb * v));
+          const T vals[3] = {store_as<T>(fdev), store_as<T>(gx), store_as<T>(gy)};
+#pragma unroll
+          for (int comp = 0; comp < 3; ++comp) {
+            T* pl = pops + (size_t)plane_of(9 * comp + i) * g.plane + o;
+            pl[0] = vals[comp];
+            if (x < 2) pl[g.nx] = vals[comp];          // ghosts of columns 0, 1 at nx, nx + 1
+            if (x >= g.nx - 2) pl[-g.nx] = vals[comp];  // ghosts of columns nx-2, nx-1 at -2, -1
+          }
+        }
       }
+      __syncthreads();
     }
   }
 }
@@ -267,15 +317,49 @@ int grid_for(long n, int threads) {
 cudaError_t launch_init_eq(int precision, void* pops, const StepGeom& g, const double* rho,
                            const double* ux, const double* uy, const double* bx, const double* by,
                            cudaStream_t s) {
-  const int grid = grid_for((long)g.nx * g.ny, 256);
+  const dim3 grid((g.nx + kInitCols - 1) / kInitCols,
+                  (unsigned)std::min((g.ny + kInitRows - 1) / kInitRows, 65535));
   if (precision == 0)
-    init_eq_kernel<double><<<grid, 256, 0, s>>>((double*)pops, g, rho, ux, uy, bx, by);
+    init_eq_kernel<double><<<grid, kInitCols, 0, s>>>((double*)pops, g, rho, ux, uy, bx, by);
   else if (precision == 1)
-    init_eq_kernel<float><<<grid, 256, 0, s>>>((float*)pops, g, rho, ux, uy, bx, by);
+    init_eq_kernel<float><<<grid, kInitCols, 0, s>>>((float*)pops, g, rho, ux, uy, bx, by);
   else if (precision == LBMHD_FP16)
-    init_eq_kernel<__half><<<grid, 256, 0, s>>>((__half*)pops, g, rho, ux, uy, bx, by);
+    init_eq_kernel<__half><<<grid, kInitCols, 0, s>>>((__half*)pops, g, rho, ux, uy, bx, by);
   else
-    init_eq_kernel<__half, true><<<grid, 256, 0, s>>>((__half*)pops, g, rho, ux, uy, bx, by);
+    init_eq_kernel<__half, true><<<grid, kInitCols, 0, s>>>((__half*)pops, g, rho, ux, uy, bx, by);
+  return cudaGetLastError();
+}
+
+// Zero the row padding of both population copies: physical columns [0, kXOff - 2) and
+// [nx + kXOff + 2, plane) of every plane row.  One thread per padding element; a warp covers a
+// row's contiguous run.  (cudaMemset2DAsync over the same 110,592 row pieces at 2048^2 took
+// 0.12 ms.)
+template <typename W>
+__global__ void zero_pads_kernel(W* __restrict__ p0, W* __restrict__ p1, StepGeom g, long rows) {
+  const int left = kXOff - 2, right0 = g.nx + kXOff + 2, padw = left + (g.plane - right0);
+  const long n = 2 * rows * padw;
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    const long rr = k / padw;
+    const int j = (int)(k - rr * padw);
+    const long row = rr < rows ? rr : rr - rows;
+    W* base = rr < rows ? p0 : p1;
+    base[(size_t)row * g.plane + (j < left ? j : right0 + (j - left))] = W(0);
+  }
+}
+
+cudaError_t launch_zero_pads(void* pops0, void* pops1, const StepGeom& g, int nplanes, size_t elem,
+                             cudaStream_t s) {
+  const long rows = (long)nplanes * g.ny;
+  const long n = 2 * rows * (kXOff - 2 + g.plane - (g.nx + kXOff + 2));
+  const int grid = grid_for(n, 256);
+  if (elem == 8)
+    zero_pads_kernel<unsigned long long><<<grid, 256, 0, s>>>((unsigned long long*)pops0,
+                                                             (unsigned long long*)pops1, g, rows);
+  else if (elem == 4)
+    zero_pads_kernel<unsigned><<<grid, 256, 0, s>>>((unsigned*)pops0, (unsigned*)pops1, g, rows);
+  else
+    zero_pads_kernel<unsigned short><<<grid, 256, 0, s>>>((unsigned short*)pops0,
+                                                         (unsigned short*)pops1, g, rows);
   return cudaGetLastError();
 }
 

@@ -43,6 +43,10 @@ struct lbmhd {
 };
 
 namespace lbmhd_gpu {
+// Implemented in lbmhd_aux.cu: zero the row padding (columns outside the interior and the two
+// ghost columns on each side) of both population copies, elements of `elem` bytes.
+cudaError_t launch_zero_pads(void* pops0, void* pops1, const StepGeom& g, int nplanes, size_t elem,
+                             cudaStream_t s);
 // Implemented in lbmhd_api.cu.
 int create_handle(lbmhd_t** out, const lbmhd_params* p);  // allocations, no initial state
 void destroy_handle(lbmhd_t* h);
