@@ -247,7 +247,6 @@ int create(lbmhd_t** out, const lbmhd_params* p) {
   // undivided differences: central a(+1)-a(-1) = 2 d; isotropic 12 d
   h->coef.kq = p->grad_stencil == LBMHD_GRAD_ISOTROPIC ? kd / 144.0 : kd / 4.0;
   h->state_bytes = (size_t)g.pitch * p->ny * h->elem;
-  const size_t ncell = (size_t)p->nx * p->ny;
 #define LB_INIT(call)                 \
   do {                                \
     cudaError_t e_ = (call);          \
