@@ -92,7 +92,11 @@ int lbmhd_params_srt(lbmhd_params* p, int nx, int ny, double nu, double eta, dou
 
 /* Create a handle and set the populations to the equilibria Eq. feq and Eq. geq of the
  * given fields (rho, u = (ux, uy), B = (bx, by)), without Delta terms.  Host input arrays
- * [ny][nx], copied; synchronises.  On error *out is NULL. */
+ * [ny][nx], read before the call returns (the caller may reuse them afterwards); synchronises.
+ * Arrays that lie wholly inside page-locked allocations (cudaHostAlloc, cudaMallocHost,
+ * cudaHostRegister) are read by the initialisation kernel directly over the host link;
+ * pageable ones are copied through a device buffer (5 x nx*ny doubles, allocated then and kept
+ * by the handle).  The state is the same either way.  On error *out is NULL. */
 int lbmhd_init(lbmhd_t** out, const lbmhd_params* p, const double* rho, const double* ux,
                const double* uy, const double* bx, const double* by);
 
@@ -112,7 +116,11 @@ int lbmhd_init_device(lbmhd_t** out, const lbmhd_params* p, const double* rho,
 int lbmhd_step(lbmhd_t* h, int nsteps);
 
 /* Macroscopic fields of the current (post-stream, pre-collision) populations: rho,
- * u = J/rho, B.  Host output arrays [ny][nx]; synchronises. */
+ * u = J/rho, B.  Host output arrays [ny][nx]; synchronises.  Arrays that lie wholly inside
+ * page-locked allocations are written by the read-out kernel directly over the host link;
+ * otherwise the fields go through a device buffer (allocated on first use, kept by the handle)
+ * and a copy.  The values are the same either way.  For FP32 / FP16 handles the sums are exact
+ * binary32 pair sums (rho and B to binary64 rounding) and u takes one binary32 division. */
 int lbmhd_moments(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx, double* by);
 
 /* Same as lbmhd_moments into device arrays [ny][nx]; asynchronous on the handle's stream. */
@@ -127,7 +135,8 @@ int lbmhd_get_populations(lbmhd_t* h, double* pops);
  * [0] sum rho  [1] sum J_x  [2] sum J_y  [3] sum B_x  [4] sum B_y
  * [5] sum rho |u|^2 / 2  [6] sum |B|^2 / 2  [7] max |div B| (isotropic stencil)
  * [8] max |div B| (central stencil)  [9] max |d_beta B_alpha| (isotropic stencil).
- * Sums are reduced in a fixed order (bitwise reproducible).  Synchronises.  Returns
+ * Sums are reduced in a fixed order (bitwise reproducible).  Synchronises; the moment fields
+ * go through the handle's device buffer (allocated on first use).  Returns
  * LBMHD_ERR_UNSTABLE (with out[] filled) if any cell has a NaN/Inf, rho <= 0 or |u| > 0.4. */
 int lbmhd_diagnostics(lbmhd_t* h, double* out);
 
