@@ -47,14 +47,17 @@ def test_checkpoint_resume_bitwise(precision):
         assert np.array_equal(other.populations(), a)
 
 
+@pytest.mark.parametrize("shape", [(96, 80), (3, 3), (261, 7), (300, 70)])
 @pytest.mark.parametrize("precision", [lbmhd.LBMHD_FP64, lbmhd.LBMHD_FP32, lbmhd.LBMHD_FP16,
                                        lbmhd.LBMHD_FP16_REL])
-def test_page_locked_host_arrays_give_the_same_bits(precision):
-    """Page-locked initial fields (copied while the handle allocates) and page-locked outputs
-    (written by the read-out kernel directly) give the same state and moments as pageable ones,
-    also for output arrays at offsets inside one page-locked block."""
+def test_page_locked_host_arrays_give_the_same_bits(precision, shape):
+    """Page-locked initial fields (read by the initialisation kernel directly) and page-locked
+    outputs (written by the read-out kernel directly) give the same state and moments as pageable
+    ones, also for output arrays at offsets inside one page-locked block; ragged grids cover
+    partial column strips and row bands of the initialisation.  The row padding of the state is
+    zero."""
     import torch
-    nx, ny = 96, 80
+    nx, ny = shape
     fields = smooth_random_fields(nx, ny, seed=12, amp_u=0.04, amp_b=0.03, amp_rho=0.01)
     pin_in = torch.empty((5, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
     pin_in[...] = np.stack(fields)
@@ -65,6 +68,14 @@ def test_page_locked_host_arrays_give_the_same_bits(precision):
         a.step(23)
         b.step(23)
         assert np.array_equal(a.populations(), b.populations())
+        state = b.get_state()
+        assert np.array_equal(a.get_state(), state)
+        # state rows: [ny][planes][plane] elements; columns [0, 30) and [nx + 34, plane) are pad
+        elem = {lbmhd.LBMHD_FP64: 8, lbmhd.LBMHD_FP32: 4}.get(precision, 2)
+        planes = 29 if precision == lbmhd.LBMHD_FP16_REL else 27
+        plane = (nx + 34 + 31) // 32 * 32
+        rows = state.view(np.dtype(f"u{elem}")).reshape(ny, planes, plane)
+        assert not rows[:, :, :30].any() and not rows[:, :, nx + 34:].any()
         want = a.moments()
         launches = b.launches
         got = b.moments(out=[block[k + 1] for k in range(5)])
