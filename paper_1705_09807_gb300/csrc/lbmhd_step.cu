@@ -1018,12 +1018,13 @@ template <int ISO, int NST, int MINB>
 __global__ void __launch_bounds__(kStepThreads / 2, MINB)
     fused_step_rel_kernel(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap usrc,
                           __half* __restrict__ dst, StepGeom g, KCoef<float> c, unsigned* __restrict__ err) {
-  if ((int)blockIdx.y * g.band >= g.ny) return;  // uniform per block
+  int strip, band;
+  tile_of_block(strip, band);
+  if (band * g.band >= g.ny) return;  // uniform per block
   init_stage_barriers(step_smem<__half, NST, true>(), &src, &usrc);
   grid_dependency_wait();
   uint32_t kbase = 0;
-  run_tile_pair<ISO, NST, true>(&src, dst, g, c, blockIdx.x * kStepThreads, blockIdx.y * g.band, blockIdx.y, kbase,
-                                err, &usrc);
+  run_tile_pair<ISO, NST, true>(&src, dst, g, c, strip * kStepThreads, band * g.band, band, kbase, err, &usrc);
 }
 
 // Ensemble: every member grid advances one step in this launch.  work[i] = {member, x0, y0,
