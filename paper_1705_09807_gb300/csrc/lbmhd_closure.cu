@@ -216,14 +216,21 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
 constexpr int kTT = 16;                       // output tile side
 constexpr int kPS = kTT + 6;                  // patch side: 22
 constexpr int kPatch = kPS * kPS;             // 484 cells
-constexpr int kMT = 4;                        // M tiles of layers 1 and 2: cells 0 .. 511
-constexpr int kL3First = 64, kL3Tiles = 3;    // layer 3: cells 64 .. 447 (rows / cols 3 .. 18)
+constexpr int kMT = 4;                        // M tiles of every layer: cells 0 .. 511
 constexpr int kPadCells = 24;                 // zero cells before and after each chunk (>= kPS + 1)
 constexpr int kChunkCells = kPadCells + kMT * 128 + kPadCells;  // 560
 constexpr int kChunkBytes = kChunkCells * 16;                   // 8960
 constexpr int kW1Bytes = 9 * 1 * 32 * 32;     // taps x K chunks x (N rows x 32 B)
 constexpr int kW2Bytes = 9 * 2 * 32 * 32;
-constexpr int kW3Bytes = 9 * 2 * 16 * 32;
+// Layer 3 multiplies the unshifted activations once by all nine taps' weights: N = 48 rows
+// n = 4 tap + co (36 used), per K chunk; the epilogue sums the nine shifted partial products.
+constexpr int kN3 = 48;
+constexpr int kW3Bytes = 2 * kN3 * 32;
+// partial products P[4 tap + co][cell - kP3Lo] (binary32) for the cells that the kept outputs
+// (patch rows / cols 3 .. 18) reach through a tap: 3 kPS + 3 - (kPS + 1) .. 18 kPS + 18 + kPS + 1
+constexpr int kP3Lo = 3 * kPS + 3 - (kPS + 1);                  // 46
+constexpr int kP3Rows = (18 * kPS + 18 + kPS + 1) - kP3Lo + 1;  // 392
+constexpr int kP3Cols = 36;
 constexpr int kWBytes = kW1Bytes + kW2Bytes + kW3Bytes;         // 36864
 constexpr int kBiasFloats = 32 + 32 + 16;
 constexpr int kPackedBytes = kWBytes + kBiasFloats * 4;         // weights then biases
@@ -236,12 +243,14 @@ constexpr int kSmBar = kSmBias + (kBiasFloats + 4 + 12) * 4;  // layer barrier, 
 constexpr int kSmSlot = kSmBar + 16;
 constexpr int kNetSmemBytes = kSmSlot + 8 + 128;      // + alignment slack
 constexpr int kMS = kPS + 2;                          // moment grid side for the features: 24
-constexpr uint32_t kTmemCols = 128;                   // 4 M tiles x 32 fp32 columns
+constexpr uint32_t kTmemCols = 256;  // layers 1, 2: 4 M tiles x 32 fp32 columns; layer 3: 4 x 48
 constexpr int kNetThreads = 256;  // 8 warps: warps w and w + 4 share TMEM lanes 32 (w % 4) ..
 static_assert(kSmBar % 8 == 0, "mbarrier alignment");
 static_assert(5 * kMS * kMS * 4 <= 4 * kChunkBytes, "moments fit in the layer-1 output buffer");
 static_assert(kPadCells >= kPS + 1, "shifted reads stay inside a chunk");
-static_assert(kL3First + 128 * kL3Tiles > (kPS - 4) * kPS + kPS - 4, "layer-3 tiles cover the output");
+static_assert(kP3Lo >= 0 && kP3Lo + kP3Rows <= kMT * 128, "layer-3 partial products lie in the M tiles");
+static_assert(kP3Cols * kP3Rows * 4 <= 8 * kChunkBytes, "layer-3 partial products fit in the activation buffers");
+static_assert(kMT * kN3 <= (int)kTmemCols, "layer-3 accumulators fit in the TMEM allocation");
 
 // Weights and biases of the three layers in the shared-memory layout above (bf16 weights,
 // fp32 biases, zero padding for ci >= CI and co >= CO).
@@ -259,13 +268,22 @@ __global__ void pack_net_kernel(const float* __restrict__ params, unsigned char*
       bias[j] = co < CO ? params[base + CO * CI * 9 + co] : 0.f;
       continue;
     }
-    int byte = 2 * i, N, nkc, CI, CO, base;
+    int byte = 2 * i;
+    if (byte >= kW1Bytes + kW2Bytes) {
+      // layer 3: per K chunk one N = 48 block, row n = 4 tap + co
+      byte -= kW1Bytes + kW2Bytes;
+      const int kc = byte / (kN3 * 32), in = byte % (kN3 * 32);
+      const int n = (in / 256) * 8 + (in % 128) / 16;
+      const int k = ((in % 256) / 128) * 8 + (in % 16) / 2;
+      const int tap = n / kC3, co = n % kC3, ci = 16 * kc + k;
+      w[i] = __float2bfloat16_rn(n < 9 * kC3 && ci < kC2 ? params[kP1 + kP2 + co * kC2 * 9 + ci * 9 + tap] : 0.f);
+      continue;
+    }
+    int N, nkc, CI, CO, base;
     if (byte < kW1Bytes) {
       N = 32, nkc = 1, CI = kC0, CO = kC1, base = 0;
-    } else if (byte < kW1Bytes + kW2Bytes) {
-      N = 32, nkc = 2, CI = kC1, CO = kC2, base = kP1, byte -= kW1Bytes;
     } else {
-      N = 16, nkc = 2, CI = kC2, CO = kC3, base = kP1 + kP2, byte -= kW1Bytes + kW2Bytes;
+      N = 32, nkc = 2, CI = kC1, CO = kC2, base = kP1, byte -= kW1Bytes;
     }
     const int blk = byte / (N * 32), in = byte % (N * 32);
     const int tap = blk / nkc, kc = blk % nkc;
@@ -315,6 +333,59 @@ __device__ __forceinline__ void issue_layer(uint32_t sbase, int act_off, int w_o
     }
   }
   tc_commit(bar);
+}
+
+// Layer 3 (32 -> 4 channels): per M tile and K chunk ONE MMA of the unshifted activations by the
+// N = 48 block of all nine taps' weights (row n = 4 tap + co), into TMEM columns mt * 48.  Column
+// 4 t + co of row m then holds the tap-t partial product sum_k A[m][k] W_t[co][k]; the output at
+// cell c is sum_t D[c + shift_t][4 t + co] (layer3_epilogue).  The nine shifted MMAs per chunk of
+// the other layers re-read the activations nine times from shared memory, the bound of their
+// phases; with four output channels that re-read cost layer 3 54 MMAs for 8 here.
+__device__ __forceinline__ void issue_layer3(uint32_t sbase, int act_off, int w_off, uint32_t tmem, uint64_t* bar) {
+  constexpr uint32_t idesc = idesc_bf16_f32(128, kN3);
+  const uint64_t a0 = smem_desc(sbase + act_off + kPadCells * 16, kChunkBytes, 128);
+  const uint64_t b0 = smem_desc(sbase + w_off, 128, 256);
+#pragma unroll
+  for (int mt = 0; mt < kMT; ++mt) {
+#pragma unroll
+    for (int kc = 0; kc < 2; ++kc) {
+      const uint64_t a = a0 + (uint64_t)(mt * 128 + 2 * kc * (kChunkBytes / 16));
+      const uint64_t b = b0 + (uint64_t)(kc * kN3 * 2);
+      tc_mma_bf16(tmem + mt * kN3, a, b, idesc, kc != 0);
+    }
+  }
+  tc_commit(bar);
+}
+
+// Layer-3 partial products TMEM -> shared memory P[col][cell - kP3Lo] (binary32, col = 4 tap +
+// co < 36), for the cells kP3Lo .. kP3Lo + kP3Rows - 1.  Warp w reads the 32 lanes of quarter
+// w % 4; warps 0-3 take columns 0-15 and 32-35, warps 4-7 columns 16-31.
+__device__ __forceinline__ void layer3_partials(uint32_t tmem, float* __restrict__ P) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = warp >> 2;
+#pragma unroll 1
+  for (int mt = 0; mt < kMT; ++mt) {
+    const uint32_t t = tmem + ((uint32_t)(32 * quarter) << 16) + mt * kN3;
+    const int row = mt * 128 + 32 * quarter + lane - kP3Lo;
+    const bool keep = row >= 0 && row < kP3Rows;
+    uint32_t r[16];
+    tmem_ld16(t + 16 * half, r);
+    if (half == 0) {
+      uint32_t q[4];
+      tmem_ld4(t + 32, q);
+      tmem_ld_wait();
+      if (keep) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) P[(32 + j) * kP3Rows + row] = __uint_as_float(q[j]);
+      }
+    } else {
+      tmem_ld_wait();
+    }
+    if (keep) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) P[(16 * half + j) * kP3Rows + row] = __uint_as_float(r[j]);
+    }
+  }
 }
 
 // Epilogue of a hidden layer: tanh(D + b) of this thread's cell in each M tile -> bf16 chunks.
@@ -459,7 +530,7 @@ __global__ void __launch_bounds__(kNetThreads, 2)
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kSmBar);
   uint64_t* wbar = bar + 1;
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + kSmSlot);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
 
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -536,22 +607,30 @@ __global__ void __launch_bounds__(kNetThreads, 2)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    // layer 3: 32 -> 4 (N = 16), only the M tiles that hold the kept outputs
-    if (tid == 0) issue_layer<16, 2, kL3First, kL3Tiles>(sbase, kSmXA, kSmW + kW1Bytes + kW2Bytes, tmem, bar);
+    // layer 3: 32 -> 4, one N = 48 MMA per M tile and K chunk, taps summed below
+    if (tid == 0) issue_layer3(sbase, kSmXA, kSmW + kW1Bytes + kW2Bytes, tmem, bar);
     if (!(ok = wait_layer(bar, phase, true))) break;
-#pragma unroll 1
-    for (int mt = 0; mt < kL3Tiles && warp < 4; ++mt) {  // warps 0-3: one cell per lane
-      uint32_t r[4];
-      tmem_ld4(tmem + ((uint32_t)(32 * warp) << 16) + mt * 16, r);
-      tmem_ld_wait();
-      const int cell = kL3First + mt * 128 + 32 * warp + lane;
-      const int pr = cell / kPS, pc = cell % kPS;
+    // the MMAs have read the activations: their buffers (XA, X1) now hold the partial products
+    float* P = reinterpret_cast<float*>(sm + kSmXA);
+    layer3_partials(tmem, P);
+    __syncthreads();
+    {  // one kept cell per thread: patch row / col 3 + tid / 16, 3 + tid % 16
+      static_assert(kNetThreads == kTT * kTT, "one output cell per thread");
+      const int pr = 3 + tid / kTT, pc = 3 + tid % kTT;
       const int gy = ty0 + pr - 3, gx = tx0 + pc - 3;
-      if (pr >= 3 && pr < 3 + kTT && pc >= 3 && pc < 3 + kTT && gy < H && gx < W) {
+      if (gy < H && gx < W) {
+        const int c = pr * kPS + pc - kP3Lo;
         float* ob = out + (size_t)b * kC3 * plane + (size_t)gy * W + gx;
 #pragma unroll
-        for (int co = 0; co < kC3; ++co)
-          ob[co * plane] = (__uint_as_float(r[co]) + bias[64 + co]) * bias[kBiasFloats + co];
+        for (int co = 0; co < kC3; ++co) {
+          float acc = 0.f;
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap) {
+            const int shift = (tap / 3 - 1) * kPS + (tap % 3 - 1);
+            acc += P[(kC3 * tap + co) * kP3Rows + c + shift];
+          }
+          ob[co * plane] = (acc + bias[64 + co]) * bias[kBiasFloats + co];
+        }
       }
     }
     // TMEM reads and shared-memory operands of this tile are finished before the next tile
