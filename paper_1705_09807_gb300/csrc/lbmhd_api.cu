@@ -435,8 +435,6 @@ int lbmhd_init(lbmhd_t** out, const lbmhd_params* p, const double* rho, const do
       free_all(h);
       return rc;
     }
-  }
-  if (!mapped)
     for (int k = 0; k < 5; ++k) {
       in[k] = h->fields + k * ncell;
       cudaError_t e = cudaMemcpyAsync(h->fields + k * ncell, src[k], ncell * sizeof(double),
@@ -447,6 +445,7 @@ int lbmhd_init(lbmhd_t** out, const lbmhd_params* p, const double* rho, const do
         return rc;
       }
     }
+  }
   cudaError_t e = launch_init_eq(h->precision, h->pops[0], h->geom, in[0], in[1], in[2], in[3],
                                  in[4], h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
